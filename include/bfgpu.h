@@ -1,0 +1,247 @@
+/*
+ * bfgpu.h -- C ABI of the GB300 (sm_103a) library for the generalized
+ * Bellman-Ford method of symbolic optimal control
+ * (Weber, Kreuzer, Knoll, arXiv 2001.06231).
+ *
+ * The library solves optimal control problems (X, U, F, G, g) of Def. ocp
+ * (Sec. III-C) whose system (X, U, F) is a discrete abstraction of a sampled
+ * system (Def. abstraction, Sec. V-A/V-B): X is a uniform grid of
+ * hyper-rectangular cells, U a finite input set, and F(x,u) an integer box of
+ * cells (the cells that meet a box over-approximation of the attainable set).
+ * It computes the value function V of Eq. (valuefunction) and a controller mu
+ * realizing it with Algorithm 1 (generalized Bellman-Ford-Yen), on one GPU.
+ *
+ * Conventions shared by every call
+ *   - Cells: D <= 4 dimensions, n[d] cells each (n[d] <= 16383), cell index
+ *     c = i0 + n0*(i1 + n1*(i2 + n2*i3)) (dim 0 fastest).  A periodic
+ *     dimension wraps (index n[d] is index 0).
+ *   - Boxes (external layout): int16 [C][U][2][D] -- lo[0..D-1] then
+ *     hi[0..D-1].  F(x,u) = { y : lo_d <= y_d <= hi_d for all d }; on a
+ *     periodic dim hi may exceed n-1 (at most lo + n - 1) and indices wrap.
+ *     lo[0] == BF_BLOCKED marks a pair whose image leaves the grid: its
+ *     successor is the overflow set of the cover (Sec. V-B), value +inf.
+ *   - Costs: G is double [C][U]: the running cost g(x,y,u) = G(x,u) for every
+ *     successor y (Eq. cost with g independent of y).  +inf is allowed (an
+ *     unusable input); NaN, -inf and finite |G| > 2^64 are rejected.  -0.0 is
+ *     read as +0.0.  The terminal cost of Eq. (cost) is 0 on target cells and
+ *     +inf elsewhere, or an explicit double [C] array (bf_solve_opts).
+ *   - Avoid cells: g(x,.,.) = g(.,x,.) = +inf and terminal +inf, so V = +inf
+ *     there and any box touching one yields +inf.
+ *   - Output: V double [C]; mu uint8 [C] with BF_HANDOVER (0xFF) meaning
+ *     "mu(x) = U", i.e. hand over control (Ex. ex:algorithm); iters = number
+ *     of passes of Algorithm 1's while-loop; status BF_CONVERGED (F1 empty:
+ *     V is the value function, Thm. BellmanFord), BF_NEG_CYCLE (the |X| cap
+ *     of the while-loop was reached: negative-cycle test) or BF_ITER_CAP
+ *     (a smaller caller cap was reached).
+ *   - Rounds are synchronous (Jacobi): every relaxation of a pass reads V as
+ *     it stood when the pass began; mu(x) changes only on a strict decrease
+ *     and takes the lowest input index among equal minima.  V, mu, iters and
+ *     status are therefore deterministic.
+ *   - Pointers: unless stated otherwise, an array argument may be host memory
+ *     or device memory of the current device (detected with
+ *     cudaPointerGetAttributes).  The caller owns every buffer it passes and
+ *     keeps it alive until the call returns; library-owned objects
+ *     (abstractions, servers) are freed only by abs_free / bf_serve_close.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Calls returning results in host memory synchronize that stream.
+ *   - Errors: every int-returning call returns BF_OK (0) or a negative
+ *     BF_ERR_* code and sets a thread-local message (bf_last_error).  No C++
+ *     exception crosses this boundary.
+ */
+#ifndef BFGPU_H
+#define BFGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BF_API __attribute__((visibility("default")))
+#else
+#define BF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BF_OK 0
+#define BF_ERR_INVALID (-1)      /* bad argument, malformed box, NaN cost   */
+#define BF_ERR_OOM (-2)          /* device allocation failed / over budget  */
+#define BF_ERR_CUDA (-3)         /* a CUDA runtime call failed              */
+#define BF_ERR_TIMEOUT (-4)      /* a bounded device wait gave up           */
+#define BF_ERR_UNSUPPORTED (-5)  /* valid but not supported by this build   */
+
+#define BF_CONVERGED 0
+#define BF_NEG_CYCLE 1
+#define BF_ITER_CAP 2
+
+#define BF_HANDOVER 0xFF
+#define BF_BLOCKED (-32768)
+
+/* Built-in sampled systems (Sec. V, Eq. ode).  Parameters in bf_dynamics.param:
+ *   BF_DYN_LINEAR2D   double integrator x0' = x1, x1' = u0; exact linear flow
+ *                     of the cell corners (no parameters).
+ *   BF_DYN_UNICYCLE3D x' = v cos th, y' = v sin th, th' = w; u = (v, w);
+ *                     param[0] = disturbance bound (added to every component).
+ *   BF_DYN_FIRE4D     x' = V cos psi + param[0], y' = V sin psi,
+ *                     psi' = (param[1] / V) tan(phi), V' = a; u = (phi, a);
+ *                     param[2], param[3] = lower / upper speed bound used in
+ *                     the Jacobian bound; param[4] = disturbance bound.
+ * UNICYCLE3D and FIRE4D boxes are centre +- growth bound: the classical RK4
+ * scheme (rk4_substeps equal steps) applied to x' = f(x,u) from the cell
+ * centre and to r' = L r + w from r(0) = eta/2 (Sec. V-B, box
+ * over-approximation of attainable sets).  Cells meeting [a, b] on dim d are
+ * floor((a - lo_d)/eta_d) .. floor((b - lo_d)/eta_d). */
+#define BF_DYN_LINEAR2D 1
+#define BF_DYN_UNICYCLE3D 2
+#define BF_DYN_FIRE4D 3
+
+/* Storage mode of an abstraction (Sec. IV-B, memory control): STORED keeps the
+ * image of F in device memory; RECOMPUTE keeps only the dynamics and
+ * regenerates each box inside the relaxation kernel (bit-identical boxes,
+ * 4*D*C*U fewer bytes, far more FP64 work). */
+#define BF_MODE_STORED 0
+#define BF_MODE_RECOMPUTE 1
+
+typedef struct {
+    int32_t ndim;          /* D, 1..4                                   */
+    int32_t n[4];          /* cells per dimension                       */
+    double lo[4], hi[4];   /* grid extent: cell k of dim d spans
+                              [lo + k*eta, lo + (k+1)*eta], eta=(hi-lo)/n */
+    uint8_t periodic[4];   /* nonzero: the dimension wraps              */
+} bf_grid;
+
+typedef struct {
+    int32_t ninputs;       /* |U'|, 1..254                              */
+    int32_t udim;          /* components per input                      */
+    const double *u;       /* host, row-major [ninputs][udim]           */
+} bf_inputs;
+
+typedef struct {
+    int32_t kind;          /* BF_DYN_*                                  */
+    int32_t rk4_substeps;  /* RK4 steps per sampling period (>= 1)      */
+    double param[8];
+} bf_dynamics;
+
+typedef struct bf_abstraction bf_abstraction;   /* opaque, device-resident */
+
+/* abs_build -- discrete abstraction of the sampled system (dyn, tau) on grid
+ * with the given inputs (Def. abstraction, Sec. V-B).  Writes, per (cell,
+ * input), the int16 successor box on the device, then the predecessor index
+ * (a per-cell bounding box of pred(y) = {x : y in F(x,u) for some u}, a
+ * superset of Eq. pred, which Sec. V-B allows).  mode = BF_MODE_STORED or
+ * BF_MODE_RECOMPUTE.  On success *out owns all device memory (abs_free).
+ * Errors: BF_ERR_INVALID (grid/inputs/dyn out of range), BF_ERR_OOM,
+ * BF_ERR_CUDA. */
+BF_API int abs_build(const bf_dynamics *dyn, const bf_grid *grid, const bf_inputs *inputs,
+              double tau, int32_t mode, void *stream, bf_abstraction **out);
+
+/* abs_from_boxes -- abstraction from caller-supplied boxes in the external
+ * layout int16 [C][U][2][D] (host or device).  Every box is validated on the
+ * device (0 <= lo <= hi <= n-1, or hi <= lo + n - 1 on a periodic dim, or
+ * blocked); any malformed box gives BF_ERR_INVALID.  Always STORED mode. */
+BF_API int abs_from_boxes(const bf_grid *grid, int32_t ninputs, const int16_t *boxes,
+                   void *stream, bf_abstraction **out);
+
+/* abs_export_boxes -- write the abstraction's boxes to out (int16
+ * [C][U][2][D], host or device).  In RECOMPUTE mode the boxes are generated
+ * by the same device code the solver uses. */
+BF_API int abs_export_boxes(const bf_abstraction *abs, int16_t *out, void *stream);
+
+/* abs_export_pred -- write the predecessor index to out (int16 [C][2][D]):
+ * offsets lo then hi, x in pred(y) only if y + lo <= x <= y + hi per dim (on a
+ * periodic dim the offsets are taken mod n).  lo[0] > hi[0] = empty. */
+BF_API int abs_export_pred(const bf_abstraction *abs, int16_t *out, void *stream);
+
+/* abs_info -- sizes of an abstraction; any out pointer may be NULL. */
+BF_API int abs_info(const bf_abstraction *abs, int64_t *ncells, int32_t *ninputs,
+             int32_t *ndim, int32_t *mode, int64_t *device_bytes);
+
+/* abs_free -- release an abstraction (NULL is a no-op).  The caller must not
+ * free it while a solve on it is running. */
+BF_API void abs_free(bf_abstraction *abs);
+
+#define BF_SCHED_AUTO 0
+#define BF_SCHED_SEGMENT 1     /* warp per 32 consecutive cells (lanes = cells) */
+#define BF_SCHED_LIST 2        /* warp per cells in a list (lanes = inputs)     */
+
+#define BF_FLAG_HOST_LOOP 1    /* drive rounds from the host (debugging)        */
+
+typedef struct {
+    int64_t max_iters;         /* 0 -> |X| (the paper's cap); else min(., |X|) */
+    int32_t schedule;          /* BF_SCHED_*                                    */
+    int32_t flags;             /* BF_FLAG_*                                     */
+    const double *terminal;    /* optional [C] terminal cost (host or device);
+                                  NULL -> 0 on target cells, +inf elsewhere     */
+    int64_t *trace;            /* optional host [trace_cap][4]: per pass |F1|
+                                  (cells relaxed), changed cells, active
+                                  segments, executed (cell,input) pairs         */
+    int64_t trace_cap;
+} bf_solve_opts;
+
+/* bf_solve -- Algorithm 1 (Sec. IV-A) on the abstraction with running cost G
+ * ([C][U] double), target ([C] uint8, nonzero = terminal cost 0; ignored when
+ * opts->terminal is set) and avoid ([C] uint8 or NULL).  Writes V ([C]
+ * double), mu ([C] uint8), *iters and *status (host pointers for the last
+ * two).  V and mu may be host or device.  opts may be NULL.  One solve at a
+ * time per abstraction handle (they share its workspace).
+ * Errors: BF_ERR_INVALID (NaN / -inf / too large costs, bad sizes),
+ * BF_ERR_OOM, BF_ERR_CUDA. */
+BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *target,
+             const uint8_t *avoid, const bf_solve_opts *opts, double *V, uint8_t *mu,
+             int64_t *iters, int32_t *status, void *stream);
+
+/* bf_solve_batch -- n independent instances of bf_solve (possibly on
+ * different abstractions of uneven size), advanced together: every device
+ * step relaxes the frontiers of all unfinished instances in one launch.
+ * Arrays of n pointers (host arrays of pointers; the pointed-to buffers as in
+ * bf_solve).  avoid[i] may be NULL; terminal may be NULL or hold NULLs.
+ * Results are identical to n separate bf_solve calls. */
+BF_API int bf_solve_batch(int32_t n, const bf_abstraction *const *abs, const double *const *G,
+                   const uint8_t *const *target, const uint8_t *const *avoid,
+                   const double *const *terminal, int64_t max_iters,
+                   double *const *V, uint8_t *const *mu, int64_t *iters, int32_t *status,
+                   void *stream);
+
+/* Server: continuous batching of solve requests on resident abstractions.
+ * Requests are admitted while the device-memory budget and the slot count
+ * allow; the engine advances all admitted instances together, retires
+ * finished ones and admits waiting ones between device steps. */
+typedef struct bf_server bf_server;
+
+typedef struct {
+    const bf_abstraction *abs;   /* resident abstraction (kept alive by caller) */
+    const double *G;             /* host [C][U], copied at submit               */
+    const uint8_t *target;       /* host [C] or NULL when terminal is given     */
+    const uint8_t *avoid;        /* host [C] or NULL                            */
+    const double *terminal;      /* host [C] or NULL                            */
+    int64_t max_iters;
+    double *V;                   /* host [C] destination, written on completion */
+    uint8_t *mu;                 /* host [C] destination                        */
+} bf_request;
+
+typedef struct {
+    int32_t done;                /* 1 when V/mu/iters/status are final           */
+    int32_t status;
+    int64_t iters;
+    int32_t error;               /* BF_OK or the error of this request           */
+    double submit_s, admit_s, finish_s;   /* wall clock (seconds, monotonic)    */
+} bf_result;
+
+/* bf_serve_open -- start a server with a device-memory budget in bytes for
+ * per-request state and at most max_active concurrently admitted requests. */
+BF_API int bf_serve_open(size_t hbm_budget, int32_t max_active, void *stream, bf_server **out);
+/* bf_serve_submit -- enqueue a request (inputs copied); returns its id. */
+BF_API int bf_serve_submit(bf_server *srv, const bf_request *req, uint64_t *id);
+/* bf_serve_poll -- state of request id; wait != 0 blocks until done. */
+BF_API int bf_serve_poll(bf_server *srv, uint64_t id, int32_t wait, bf_result *out);
+/* bf_serve_close -- finish all requests and free the server. */
+BF_API void bf_serve_close(bf_server *srv);
+
+/* bf_last_error -- message of the last failed call on this thread. */
+BF_API const char *bf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFGPU_H */

@@ -1,0 +1,250 @@
+"""Generalized Bellman-Ford for symbolic optimal control on GB300 (sm_103a).
+
+Python binding of the C ABI declared in ``include/bfgpu.h`` (arXiv
+2001.06231, Algorithm 1 and the abstraction of Sec. V-B).  This module only
+marshals arguments with ctypes: every step of the method runs in the CUDA
+library ``_build/libbfgpu.so``.  There is no CPU fallback: if the library
+cannot be loaded, the first call raises.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); outputs are numpy arrays unless CUDA tensors are passed as
+destinations.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+BF_OK = 0
+BF_ERR = {-1: "BF_ERR_INVALID", -2: "BF_ERR_OOM", -3: "BF_ERR_CUDA", -4: "BF_ERR_TIMEOUT",
+          -5: "BF_ERR_UNSUPPORTED"}
+CONVERGED, NEG_CYCLE, ITER_CAP = 0, 1, 2
+HANDOVER = 0xFF
+BLOCKED = -32768
+LINEAR2D, UNICYCLE3D, FIRE4D = 1, 2, 3
+MODE_STORED, MODE_RECOMPUTE = 0, 1
+SCHED_AUTO, SCHED_SEGMENT, SCHED_LIST = 0, 1, 2
+FLAG_HOST_LOOP = 1
+
+EXPORTED = ["abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
+            "abs_free", "bf_solve", "bf_last_error"]
+
+
+class BfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (BF_ERR.get(code, "BF_ERR"), code, msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 4), ("lo", ctypes.c_double * 4),
+                ("hi", ctypes.c_double * 4), ("periodic", ctypes.c_uint8 * 4)]
+
+
+class Inputs(ctypes.Structure):
+    _fields_ = [("ninputs", ctypes.c_int32), ("udim", ctypes.c_int32), ("u", ctypes.c_void_p)]
+
+
+class Dynamics(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("rk4_substeps", ctypes.c_int32), ("param", ctypes.c_double * 8)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int64), ("schedule", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("terminal", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("abs", ctypes.c_void_p), ("G", ctypes.c_void_p), ("target", ctypes.c_void_p),
+                ("avoid", ctypes.c_void_p), ("terminal", ctypes.c_void_p), ("max_iters", ctypes.c_int64),
+                ("V", ctypes.c_void_p), ("mu", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("iters", ctypes.c_int64),
+                ("error", ctypes.c_int32), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("finish_s", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building first if stale) the CUDA library; raises if unavailable."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or os.environ.get("BFGPU_REBUILD"):
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        missing = [name for name in EXPORTED if not hasattr(L, name)]
+        if missing:
+            raise BfError(-5, "library %s lacks %s" % (path, ", ".join(missing)))
+        P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.abs_build.argtypes = [P, P, P, f64, i32, P, P]
+        L.abs_from_boxes.argtypes = [P, i32, P, P, P]
+        L.abs_export_boxes.argtypes = [P, P, P]
+        L.abs_export_pred.argtypes = [P, P, P]
+        L.abs_info.argtypes = [P, P, P, P, P, P]
+        L.abs_free.argtypes = [P]
+        L.abs_free.restype = None
+        L.bf_solve.argtypes = [P, P, P, P, P, P, P, P, P, P]
+        L.bf_last_error.restype = ctypes.c_char_p
+        for name in ("abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
+                     "bf_solve"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != BF_OK:
+        raise BfError(rc, lib().bf_last_error().decode())
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array / torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()            # torch tensor
+
+
+def _host(a, dtype):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=dtype)
+    return a.contiguous()          # torch tensor, host or device; dtype is the caller's
+
+
+def _stream(s):
+    if s is None:
+        return None
+    return getattr(s, "cuda_stream", s)
+
+
+def make_grid(n, lo=None, hi=None, periodic=None):
+    """bf_grid from per-dimension lists (or an object with n/lo/hi/periodic)."""
+    if isinstance(n, Grid):
+        return n
+    if hasattr(n, "n"):
+        g = n
+        n, lo, hi, periodic = g.n, g.lo, g.hi, g.periodic
+    D = len(n)
+    lo = lo if lo is not None else [0.0] * D
+    hi = hi if hi is not None else [float(k) for k in n]
+    periodic = periodic if periodic is not None else [False] * D
+    s = Grid()
+    s.ndim = D
+    for d in range(D):
+        s.n[d] = int(n[d])
+        s.lo[d] = float(lo[d])
+        s.hi[d] = float(hi[d])
+        s.periodic[d] = 1 if periodic[d] else 0
+    return s
+
+
+class Abstraction:
+    """Device-resident discrete abstraction (handle of the C ABI)."""
+
+    def __init__(self, handle, grid):
+        self.handle = ctypes.c_void_p(handle)
+        self.grid = grid
+        nc, nu, nd, md, nb = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(),
+                              ctypes.c_int64())
+        _check(lib().abs_info(self.handle, ctypes.byref(nc), ctypes.byref(nu), ctypes.byref(nd),
+                              ctypes.byref(md), ctypes.byref(nb)))
+        self.ncells, self.ninputs, self.ndim = nc.value, nu.value, nd.value
+        self.mode, self.device_bytes = md.value, nb.value
+
+    def export_boxes(self, out=None, stream=None):
+        if out is None:
+            out = np.empty((self.ncells, self.ninputs, 2, self.ndim), dtype=np.int16)
+        _check(lib().abs_export_boxes(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def export_pred(self, out=None, stream=None):
+        if out is None:
+            out = np.empty((self.ncells, 2, self.ndim), dtype=np.int16)
+        _check(lib().abs_export_pred(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().abs_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def abs_build(kind, params, substeps, grid, inputs, tau, mode=MODE_STORED, stream=None):
+    """Build the abstraction of a built-in sampled system on the device."""
+    g = make_grid(grid)
+    u = np.ascontiguousarray(np.atleast_2d(inputs), dtype=np.float64)
+    inp = Inputs(u.shape[0], u.shape[1], u.ctypes.data)
+    dyn = Dynamics()
+    dyn.kind = int(kind)
+    dyn.rk4_substeps = int(substeps)
+    for i, p in enumerate(params):
+        dyn.param[i] = float(p)
+    h = ctypes.c_void_p()
+    _check(lib().abs_build(ctypes.byref(dyn), ctypes.byref(g), ctypes.byref(inp), float(tau), int(mode),
+                           _stream(stream), ctypes.byref(h)))
+    return Abstraction(h.value, g)
+
+
+def abs_build_workload(w, mode=MODE_STORED, stream=None):
+    return abs_build(w.kind, w.params, w.substeps, w.grid, w.inputs, w.tau, mode, stream)
+
+
+def abs_from_boxes(grid, boxes, stream=None):
+    """Abstraction from boxes int16 [C][U][2][D] (numpy or torch, host or device)."""
+    g = make_grid(grid)
+    b = _host(boxes, np.int16)
+    U = int(b.shape[1])
+    h = ctypes.c_void_p()
+    _check(lib().abs_from_boxes(ctypes.byref(g), U, _ptr(b), _stream(stream), ctypes.byref(h)))
+    return Abstraction(h.value, g)
+
+
+def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0, schedule=SCHED_AUTO,
+             host_loop=False, trace_cap=0, V=None, mu=None, stream=None):
+    """Algorithm 1 on the device.  Returns dict(V, mu, iters, status[, trace])."""
+    C = abstraction.ncells
+    Gc = _host(G, np.float64)
+    tg = _host(target, np.uint8)
+    av = _host(avoid, np.uint8)
+    tm = _host(terminal, np.float64)
+    if V is None:
+        V = np.empty(C, dtype=np.float64)
+    if mu is None:
+        mu = np.empty(C, dtype=np.uint8)
+    opts = SolveOpts()
+    opts.max_iters = int(max_iters)
+    opts.schedule = int(schedule)
+    opts.flags = FLAG_HOST_LOOP if host_loop else 0
+    opts.terminal = _ptr(tm)
+    trace = None
+    if trace_cap:
+        trace = np.zeros((int(trace_cap), 4), dtype=np.int64)
+        opts.trace = trace.ctypes.data
+        opts.trace_cap = int(trace_cap)
+    it = ctypes.c_int64()
+    st = ctypes.c_int32()
+    _check(lib().bf_solve(abstraction.handle, _ptr(Gc), _ptr(tg), _ptr(av), ctypes.byref(opts), _ptr(V),
+                          _ptr(mu), ctypes.byref(it), ctypes.byref(st), _stream(stream)))
+    out = {"V": V, "mu": mu, "iters": it.value, "status": st.value}
+    if trace is not None:
+        k = min(it.value, int(trace_cap))
+        out["trace"] = trace[:k].copy()
+    return out

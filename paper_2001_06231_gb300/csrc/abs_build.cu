@@ -1,0 +1,467 @@
+// abs_build.cu -- discrete abstraction on the device (Sec. V-B, Def.
+// abstraction) and the predecessor index of Eq. (pred), plus the abstraction
+// handle API of bfgpu.h.
+//
+// K1 build:    one thread per (cell, input), consecutive threads take
+//              consecutive cells of one input, so the [U][C] box records are
+//              written coalesced.  FP64 throughout (RK4 + growth bound).
+// K2 pred:     one thread per (cell x, input u) walks the cells y of its box
+//              and widens y's predecessor bounding box (offsets x - y per
+//              dim) with read-check-then-atomicMin/Max; the plain read skips
+//              the atomic whenever the bound already covers x (bounds only
+//              widen, so a stale read never wrongly skips).  The result is
+//              the bounding box of pred(y) = {x : exists u, y in F(x,u)}:
+//              a superset of Eq. (pred), which the algorithm tolerates (the
+//              paper notes pred may be replaced by a superset, Sec. V-B).
+// K12 check:   validation of caller-supplied boxes; counts malformed records.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "bf_internal.cuh"
+#include "dynamics.cuh"
+
+using namespace bfk;
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+namespace bfh {
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? BF_ERR_OOM : BF_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace bfh
+
+extern "C" const char* bf_last_error(void) { return bfh::g_err.c_str(); }
+
+static int grid_blocks(long long work, int threads) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long need = (work + threads - 1) / threads;
+    long long cap = (long long)sms * 16;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_build_boxes(DynDesc dd, GridDesc g, const double* __restrict__ inputs, void* boxes) {
+    const long long total = g.C * g.U;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long c = p - (long long)u * g.C;
+        Box<D> b = make_box<D>(dd, g, inputs, c, u);
+        store_box<D>(boxes, p, b);
+    }
+}
+
+// external [C][U][2][D] -> internal [U][C] records, with validation
+template <int D>
+__global__ void k_import_boxes(GridDesc g, const short* __restrict__ ext, void* boxes,
+                               unsigned long long* nbad) {
+    const long long total = g.C * g.U;
+    unsigned long long bad = 0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long c = p - (long long)u * g.C;
+        const short* e = ext + (c * g.U + u) * (2 * D);
+        Box<D> b;
+#pragma unroll
+        for (int d = 0; d < D; ++d) { b.lo[d] = e[d]; b.hi[d] = e[D + d]; }
+        if (b.lo[0] == kBlocked) {
+#pragma unroll
+            for (int d = 1; d < D; ++d) b.lo[d] = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) b.hi[d] = 0;
+        } else {
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int n = g.n[d];
+                if (b.lo[d] < 0 || b.lo[d] >= n || b.hi[d] < b.lo[d]) ok = false;
+                if (g.periodic[d]) { if (b.hi[d] - b.lo[d] + 1 > n) ok = false; }
+                else if (b.hi[d] >= n) ok = false;
+            }
+            if (!ok) {
+                ++bad;
+                b.lo[0] = kBlocked;
+            }
+        }
+        store_box<D>(boxes, p, b);
+    }
+    if (bad) atomicAdd(nbad, bad);
+}
+
+template <int D>
+__global__ void k_export_boxes(GridDesc g, DynDesc dd, const double* __restrict__ inputs,
+                               const void* __restrict__ boxes, short* ext) {
+    const long long total = g.C * g.U;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long c = p - (long long)u * g.C;
+        Box<D> b = boxes ? load_box<D>(boxes, p) : make_box<D>(dd, g, inputs, c, u);
+        short* e = ext + (c * g.U + u) * (2 * D);
+#pragma unroll
+        for (int d = 0; d < D; ++d) { e[d] = (short)b.lo[d]; e[D + d] = (short)b.hi[d]; }
+    }
+}
+
+__global__ void k_fill_i32(int* a, long long n, int v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+template <int D>
+__global__ void k_pred_scatter(GridDesc g, DynDesc dd, const double* __restrict__ inputs,
+                               const void* __restrict__ boxes, int* plo, int* phi) {
+    const long long total = g.C * g.U;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long x = p - (long long)u * g.C;
+        Box<D> b = boxes ? load_box<D>(boxes, p) : make_box<D>(dd, g, inputs, x, u);
+        if (b.lo[0] == kBlocked) continue;
+        int kx[4];
+        cell_coords(g, x, kx);
+        int len[D], cnt = 1;
+#pragma unroll
+        for (int d = 0; d < D; ++d) { len[d] = b.hi[d] - b.lo[d] + 1; cnt *= len[d]; }
+        for (int t = 0; t < cnt; ++t) {
+            int r = t;
+            long long y = 0;
+            int off[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int j = r % len[d];
+                r /= len[d];
+                int yd = b.lo[d] + j;
+                const int n = g.n[d];
+                if (g.periodic[d] && yd >= n) yd -= n;
+                y += (long long)yd * g.stride[d];
+                int o = kx[d] - yd;
+                if (g.periodic[d]) {
+                    o %= n;
+                    if (o < 0) o += n;
+                    if (o >= n - n / 2) o -= n;   // o in [-(n/2), n - n/2 - 1]
+                }
+                off[d] = o;
+            }
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                int* lo = plo + (long long)d * g.C + y;
+                int* hi = phi + (long long)d * g.C + y;
+                if (*((volatile int*)lo) > off[d]) atomicMin(lo, off[d]);
+                if (*((volatile int*)hi) < off[d]) atomicMax(hi, off[d]);
+            }
+        }
+    }
+}
+
+template <int D>
+__global__ void k_pred_pack(GridDesc g, const int* __restrict__ plo, const int* __restrict__ phi,
+                            short* pred) {
+    for (long long y = blockIdx.x * (long long)blockDim.x + threadIdx.x; y < g.C;
+         y += (long long)gridDim.x * blockDim.x) {
+        short* q = pred + y * (2 * D);
+        if (plo[y] > phi[y]) {          // no predecessor at all
+#pragma unroll
+            for (int d = 0; d < D; ++d) { q[d] = 32767; q[D + d] = -32768; }
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            q[d] = (short)plo[(long long)d * g.C + y];
+            q[D + d] = (short)phi[(long long)d * g.C + y];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host API
+// ---------------------------------------------------------------------------
+void bf_solve_ws_free(bf_solve_ws* ws);   // solve.cu
+
+static int check_grid(const bf_grid* grid, GridDesc& g) {
+    if (!grid || grid->ndim < 1 || grid->ndim > 4) {
+        bfh::set_error("grid: ndim must be 1..4");
+        return BF_ERR_INVALID;
+    }
+    memset(&g, 0, sizeof g);
+    g.D = grid->ndim;
+    long long C = 1;
+    for (int d = 0; d < g.D; ++d) {
+        if (grid->n[d] < 1 || grid->n[d] > 16383) {
+            bfh::set_error("grid: n[%d] = %d outside 1..16383", d, grid->n[d]);
+            return BF_ERR_INVALID;
+        }
+        g.n[d] = grid->n[d];
+        g.periodic[d] = grid->periodic[d] ? 1 : 0;
+        g.stride[d] = C;
+        C *= grid->n[d];
+    }
+    if (C > (1LL << 31) - 64) {
+        bfh::set_error("grid: %lld cells exceed the 2^31 cell limit", C);
+        return BF_ERR_INVALID;
+    }
+    for (int d = g.D; d < 4; ++d) { g.n[d] = 1; g.stride[d] = C; }
+    g.C = C;
+    return BF_OK;
+}
+
+static DynDesc make_dyndesc(const bf_abstraction* a) {
+    DynDesc dd;
+    memset(&dd, 0, sizeof dd);
+    dd.kind = a->dyn.kind;
+    dd.substeps = a->dyn.rk4_substeps;
+    dd.udim = a->udim;
+    dd.tau = a->tau;
+    for (int i = 0; i < 8; ++i) dd.p[i] = a->dyn.param[i];
+    for (int d = 0; d < a->g.D; ++d) {
+        dd.glo[d] = a->glo[d];
+        dd.eta[d] = (a->ghi[d] - a->glo[d]) / (double)a->g.n[d];
+    }
+    return dd;
+}
+
+static size_t box_bytes(const GridDesc& g) { return (size_t)g.C * g.U * 4 * g.D; }
+
+template <int D>
+static int build_pred_t(bf_abstraction* a, cudaStream_t st) {
+    const GridDesc& g = a->g;
+    int *plo = nullptr, *phi = nullptr;
+    BF_CUDA(cudaMallocAsync((void**)&plo, sizeof(int) * g.C * D, st));
+    BF_CUDA(cudaMallocAsync((void**)&phi, sizeof(int) * g.C * D, st));
+    k_fill_i32<<<grid_blocks(g.C * D, 256), 256, 0, st>>>(plo, g.C * D, 0x7FFFFFFF);
+    k_fill_i32<<<grid_blocks(g.C * D, 256), 256, 0, st>>>(phi, g.C * D, (int)0x80000000);
+    DynDesc dd = make_dyndesc(a);
+    k_pred_scatter<D><<<grid_blocks(g.C * g.U, 256), 256, 0, st>>>(g, dd, a->d_inputs, a->d_boxes, plo, phi);
+    k_pred_pack<D><<<grid_blocks(g.C, 256), 256, 0, st>>>(g, plo, phi, a->d_pred);
+    BF_CUDA(cudaGetLastError());
+    BF_CUDA(cudaFreeAsync(plo, st));
+    BF_CUDA(cudaFreeAsync(phi, st));
+    return BF_OK;
+}
+
+static int build_pred(bf_abstraction* a, cudaStream_t st) {
+    switch (a->g.D) {
+        case 1: return build_pred_t<1>(a, st);
+        case 2: return build_pred_t<2>(a, st);
+        case 3: return build_pred_t<3>(a, st);
+        default: return build_pred_t<4>(a, st);
+    }
+}
+
+static bf_abstraction* new_abs() {
+    bf_abstraction* a = new bf_abstraction;
+    memset(a, 0, sizeof *a);
+    cudaGetDevice(&a->device);
+    return a;
+}
+
+extern "C" void abs_free(bf_abstraction* a) {
+    if (!a) return;
+    if (a->ws) bf_solve_ws_free(a->ws);
+    cudaFree(a->d_boxes);
+    cudaFree(a->d_pred);
+    cudaFree(a->d_inputs);
+    delete a;
+}
+
+extern "C" int abs_build(const bf_dynamics* dyn, const bf_grid* grid, const bf_inputs* inputs,
+                         double tau, int32_t mode, void* stream, bf_abstraction** out) {
+    if (!out) { bfh::set_error("abs_build: out is NULL"); return BF_ERR_INVALID; }
+    *out = nullptr;
+    GridDesc g;
+    int rc = check_grid(grid, g);
+    if (rc) return rc;
+    if (!dyn || !inputs || !inputs->u || inputs->ninputs < 1 || inputs->ninputs > 254 || inputs->udim < 1) {
+        bfh::set_error("abs_build: need dyn and 1..254 inputs with udim >= 1");
+        return BF_ERR_INVALID;
+    }
+    const int need_d = dyn->kind == BF_DYN_LINEAR2D ? 2 : dyn->kind == BF_DYN_UNICYCLE3D ? 3
+                     : dyn->kind == BF_DYN_FIRE4D ? 4 : -1;
+    if (need_d < 0 || need_d != g.D) {
+        bfh::set_error("abs_build: dynamics kind %d needs a %d-D grid", dyn->kind, need_d);
+        return BF_ERR_INVALID;
+    }
+    if (dyn->kind != BF_DYN_LINEAR2D && (dyn->rk4_substeps < 1 || inputs->udim < 2)) {
+        bfh::set_error("abs_build: need rk4_substeps >= 1 and 2 input components");
+        return BF_ERR_INVALID;
+    }
+    if (!(tau > 0.0) || (mode != BF_MODE_STORED && mode != BF_MODE_RECOMPUTE)) {
+        bfh::set_error("abs_build: need tau > 0 and a valid mode");
+        return BF_ERR_INVALID;
+    }
+    for (int d = 0; d < g.D; ++d)
+        if (!(grid->hi[d] > grid->lo[d])) {
+            bfh::set_error("abs_build: grid extent of dim %d is empty", d);
+            return BF_ERR_INVALID;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    bf_abstraction* a = new_abs();
+    a->g = g;
+    a->g.U = inputs->ninputs;
+    for (int d = 0; d < g.D; ++d) { a->glo[d] = grid->lo[d]; a->ghi[d] = grid->hi[d]; }
+    a->mode = mode;
+    a->dyn = *dyn;
+    a->tau = tau;
+    a->udim = inputs->udim;
+    size_t in_bytes = sizeof(double) * inputs->ninputs * inputs->udim;
+    cudaError_t e = cudaMalloc(&a->d_inputs, in_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a->d_inputs, inputs->u, in_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&a->d_pred, sizeof(short) * 2 * g.D * g.C);
+    if (e == cudaSuccess && mode == BF_MODE_STORED) e = cudaMalloc(&a->d_boxes, box_bytes(a->g));
+    if (e != cudaSuccess) { abs_free(a); return bfh::cuda_fail(e, "abs_build allocation"); }
+    a->bytes = in_bytes + sizeof(short) * 2 * g.D * g.C + (mode == BF_MODE_STORED ? box_bytes(a->g) : 0);
+    DynDesc dd = make_dyndesc(a);
+    if (mode == BF_MODE_STORED) {
+        const int nb = grid_blocks(a->g.C * a->g.U, 128);
+        switch (g.D) {
+            case 2: k_build_boxes<2><<<nb, 128, 0, st>>>(dd, a->g, a->d_inputs, a->d_boxes); break;
+            case 3: k_build_boxes<3><<<nb, 128, 0, st>>>(dd, a->g, a->d_inputs, a->d_boxes); break;
+            default: k_build_boxes<4><<<nb, 128, 0, st>>>(dd, a->g, a->d_inputs, a->d_boxes); break;
+        }
+    }
+    rc = build_pred(a, st);
+    if (rc == BF_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = bfh::cuda_fail(e, "abs_build kernels");
+    }
+    if (rc) { abs_free(a); return rc; }
+    *out = a;
+    return BF_OK;
+}
+
+extern "C" int abs_from_boxes(const bf_grid* grid, int32_t ninputs, const int16_t* boxes,
+                              void* stream, bf_abstraction** out) {
+    if (!out || !boxes) { bfh::set_error("abs_from_boxes: NULL argument"); return BF_ERR_INVALID; }
+    *out = nullptr;
+    GridDesc g;
+    int rc = check_grid(grid, g);
+    if (rc) return rc;
+    if (ninputs < 1 || ninputs > 254) { bfh::set_error("abs_from_boxes: ninputs must be 1..254"); return BF_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    bf_abstraction* a = new_abs();
+    a->g = g;
+    a->g.U = ninputs;
+    for (int d = 0; d < g.D; ++d) { a->glo[d] = grid->lo[d]; a->ghi[d] = grid->hi[d]; }
+    a->mode = BF_MODE_STORED;
+    const size_t ext_bytes = box_bytes(a->g);
+    const short* src = reinterpret_cast<const short*>(boxes);
+    short* staged = nullptr;
+    unsigned long long* d_bad = nullptr;
+    unsigned long long h_bad = 0;
+    cudaError_t e = cudaMalloc(&a->d_boxes, box_bytes(a->g));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&a->d_pred, sizeof(short) * 2 * g.D * g.C);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && !bfh::is_device_ptr(boxes)) {
+        e = cudaMalloc((void**)&staged, ext_bytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(staged, boxes, ext_bytes, cudaMemcpyHostToDevice, st);
+        src = staged;
+    }
+    if (e != cudaSuccess) {
+        cudaFree(staged); cudaFree(d_bad); abs_free(a);
+        return bfh::cuda_fail(e, "abs_from_boxes allocation");
+    }
+    a->bytes = box_bytes(a->g) + sizeof(short) * 2 * g.D * g.C;
+    const int nb = grid_blocks(a->g.C * a->g.U, 256);
+    switch (g.D) {
+        case 1: k_import_boxes<1><<<nb, 256, 0, st>>>(a->g, src, a->d_boxes, d_bad); break;
+        case 2: k_import_boxes<2><<<nb, 256, 0, st>>>(a->g, src, a->d_boxes, d_bad); break;
+        case 3: k_import_boxes<3><<<nb, 256, 0, st>>>(a->g, src, a->d_boxes, d_bad); break;
+        default: k_import_boxes<4><<<nb, 256, 0, st>>>(a->g, src, a->d_boxes, d_bad); break;
+    }
+    e = cudaMemcpyAsync(&h_bad, d_bad, sizeof h_bad, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(staged);
+    cudaFree(d_bad);
+    if (e != cudaSuccess) { abs_free(a); return bfh::cuda_fail(e, "abs_from_boxes import"); }
+    if (h_bad) {
+        abs_free(a);
+        bfh::set_error("abs_from_boxes: %llu malformed boxes", h_bad);
+        return BF_ERR_INVALID;
+    }
+    rc = build_pred(a, st);
+    if (rc == BF_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = bfh::cuda_fail(e, "abs_from_boxes pred");
+    }
+    if (rc) { abs_free(a); return rc; }
+    *out = a;
+    return BF_OK;
+}
+
+extern "C" int abs_export_boxes(const bf_abstraction* a, int16_t* out, void* stream) {
+    if (!a || !out) { bfh::set_error("abs_export_boxes: NULL argument"); return BF_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = box_bytes(a->g);
+    const bool dev = bfh::is_device_ptr(out);
+    short* dst = reinterpret_cast<short*>(out);
+    if (!dev) BF_CUDA(cudaMallocAsync((void**)&dst, bytes, st));
+    DynDesc dd = make_dyndesc(a);
+    const int nb = grid_blocks(a->g.C * a->g.U, 128);
+    switch (a->g.D) {
+        case 1: k_export_boxes<1><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
+        case 2: k_export_boxes<2><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
+        case 3: k_export_boxes<3><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
+        default: k_export_boxes<4><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
+    }
+    BF_CUDA(cudaGetLastError());
+    if (!dev) {
+        BF_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, st));
+        BF_CUDA(cudaFreeAsync(dst, st));
+    }
+    BF_CUDA(cudaStreamSynchronize(st));
+    return BF_OK;
+}
+
+extern "C" int abs_export_pred(const bf_abstraction* a, int16_t* out, void* stream) {
+    if (!a || !out) { bfh::set_error("abs_export_pred: NULL argument"); return BF_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    BF_CUDA(cudaMemcpyAsync(out, a->d_pred, sizeof(short) * 2 * a->g.D * a->g.C, cudaMemcpyDefault, st));
+    BF_CUDA(cudaStreamSynchronize(st));
+    return BF_OK;
+}
+
+extern "C" int abs_info(const bf_abstraction* a, int64_t* ncells, int32_t* ninputs, int32_t* ndim,
+                        int32_t* mode, int64_t* device_bytes) {
+    if (!a) { bfh::set_error("abs_info: NULL abstraction"); return BF_ERR_INVALID; }
+    if (ncells) *ncells = a->g.C;
+    if (ninputs) *ninputs = a->g.U;
+    if (ndim) *ndim = a->g.D;
+    if (mode) *mode = a->mode;
+    if (device_bytes) *device_bytes = (int64_t)a->bytes;
+    return BF_OK;
+}

@@ -1,0 +1,472 @@
+// solve.cu -- bf_solve: Algorithm 1 (generalized Bellman-Ford-Yen, Sec. IV-A)
+// on one abstraction, on one GPU.
+//
+// Device state per solve (workspace, cached in the abstraction handle):
+//   Vkey, Vnew  int64 [C]   values as order-preserving keys (bf_internal.cuh)
+//   mu          uint8 [C]
+//   flag        uint8 [C]   cell belongs to the next frontier
+//   segflag     u32 [S]     segment (32 consecutive cells) is in the next list
+//   seglist     i32 [2][S]  active segments of the current / next frontier
+//   chg         i32 [C]     cells changed in the current pass
+//   Gint        f64 [U][C]  running cost, input-major (coalesced per input),
+//                           +inf on avoid cells; -0 read as +0
+// Frontiers (F1 / F2 of Algorithm 1) are the flag array plus the compacted
+// segment list; rows are never scanned whole.
+//
+// Round driver: the passes run inside one CUDA graph whose body (relax ->
+// propagate -> finish) sits in a conditional WHILE node; the finishing kernel
+// evaluates "F1 != empty and i < cap" on the device and sets the condition,
+// so a whole solve is one graph launch with no host round trip per pass.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <math_constants.h>
+
+#include "solve_core.cuh"
+
+using namespace bfk;
+
+struct bf_solve_ws {
+    long long C = 0;
+    int U = 0, D = 0;
+    int device = 0;
+    long long nseg_total = 0;
+    long long* Vkey = nullptr;
+    long long* Vnew = nullptr;
+    unsigned char* mu = nullptr;
+    unsigned char* flag = nullptr;
+    unsigned* segflag = nullptr;
+    int* seglist = nullptr;       // 2 * nseg_total
+    int* chg = nullptr;
+    double* Gint = nullptr;
+    Counters* ctr = nullptr;
+    // staging for host inputs / outputs
+    double* stage_G = nullptr;      // [C][U]
+    double* stage_T = nullptr;      // [C]
+    unsigned char* stage_tgt = nullptr;
+    unsigned char* stage_avoid = nullptr;
+    double* stage_V = nullptr;
+    long long* trace = nullptr;
+    long long trace_cap = 0;
+    // graph of the pass loop
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int relax_blocks = 0, prop_blocks = 0;
+    std::mutex mtx;
+};
+
+void bf_solve_ws_free(bf_solve_ws* w) {
+    if (!w) return;
+    if (w->exec) cudaGraphExecDestroy(w->exec);
+    if (w->graph) cudaGraphDestroy(w->graph);
+    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->mu); cudaFree(w->flag);
+    cudaFree(w->segflag); cudaFree(w->seglist); cudaFree(w->chg); cudaFree(w->Gint);
+    cudaFree(w->ctr); cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt);
+    cudaFree(w->stage_avoid); cudaFree(w->stage_V); cudaFree(w->trace);
+    delete w;
+}
+
+// ---------------------------------------------------------------------------
+// set-up kernels
+// ---------------------------------------------------------------------------
+
+// -0 -> +0; NaN, -inf and |finite| > 2^64 are errors.
+__device__ __forceinline__ bool clean_cost(double v, double& out) {
+    if (v != v) return false;
+    if (v == -CUDART_INF) return false;
+    if (v != CUDART_INF && fabs(v) > 18446744073709551616.0) return false;
+    out = (v == 0.0) ? 0.0 : v;
+    return true;
+}
+
+// Gint[u][c] = clean(G[c][u]), +inf on avoid cells.  Lanes take consecutive
+// cells of one input: the writes are coalesced and the strided reads of a
+// warp's 32 x U block are served from L1 across the u loop.
+__global__ void k_init_costs(long long C, int U, const double* __restrict__ G,
+                             const unsigned char* __restrict__ avoid, double* Gint, Counters* ctr) {
+    bool bad = false;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x) {
+        const bool av = avoid && avoid[c];
+        for (int u = 0; u < U; ++u) {
+            double v;
+            if (!clean_cost(__ldg(G + c * U + u), v)) bad = true;
+            Gint[(long long)u * C + c] = av ? CUDART_INF : v;
+        }
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+// Lines 1-9 of Algorithm 1: W = terminal cost (0 on target, +inf elsewhere,
+// or the caller's array), mu = U (hand over), and the cells with finite W go
+// to the changed list so that the first propagate builds F1 from their preds.
+__global__ void k_init_values(long long C, const double* __restrict__ terminal,
+                              const unsigned char* __restrict__ target,
+                              const unsigned char* __restrict__ avoid, long long* Vkey,
+                              long long* Vnew, unsigned char* mu, unsigned char* flag, int* chg,
+                              Counters* ctr) {
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // uniform trip count per warp so the ballot in warp_append is safe
+    const long long rounds = (C + stride - 1) / stride;
+    for (long long it = 0; it < rounds; ++it) {
+        const long long c = start + it * stride;
+        bool finite = false;
+        if (c < C) {
+            double t;
+            if (terminal) {
+                if (!clean_cost(terminal[c], t)) { bad = true; t = CUDART_INF; }
+            } else {
+                t = (target && target[c]) ? 0.0 : CUDART_INF;
+            }
+            if (avoid && avoid[c]) t = CUDART_INF;
+            const long long k = key_of(t);
+            Vkey[c] = k;
+            Vnew[c] = k;
+            mu[c] = kHandover;
+            flag[c] = 0;
+            finite = k != kKeyInf;
+        }
+        const int slot = warp_append(finite, &ctr->nchg);
+        if (finite) chg[slot] = (int)c;
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+__global__ void k_init_counters(Counters* ctr, long long cap) {
+    memset(ctr, 0, sizeof(Counters));
+    ctr->cap = cap;
+}
+
+// ---------------------------------------------------------------------------
+// pass kernels
+// ---------------------------------------------------------------------------
+template <int D, bool RECOMP>
+__global__ void __launch_bounds__(256) k_relax(InstView v) {
+    Counters* k = v.ctr;
+    if (k->done) return;
+    const int par = (int)(k->round & 1);
+    const int nseg = k->nseg[par];
+    const int* list = seglist_of(v, par);
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    long long relaxed = 0;
+    for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < nseg; s += nwarps)
+        relaxed += relax_segment<D, RECOMP>(v, list[s]);
+    if ((threadIdx.x & 31) == 0 && relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_propagate(InstView v, int init) {
+    Counters* k = v.ctr;
+    if (k->done) return;
+    const int par = init ? 0 : (int)((k->round + 1) & 1);
+    const int nchg = k->nchg;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
+        propagate_cell<D>(v, v.chg[i], par, !init);
+}
+
+// After the initial propagate: F1 is in list 0; decide whether to loop.
+__global__ void k_after_init(Counters* k, cudaGraphConditionalHandle h, int use_graph) {
+    k->nchg = 0;
+    int cont = (k->err == 0 && k->nseg[0] > 0 && k->cap > 0) ? 1 : 0;
+    if (!cont) {
+        k->done = 1;
+        k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
+    }
+    if (use_graph) cudaGraphSetConditional(h, cont);
+}
+
+__global__ void k_finish(InstView v, cudaGraphConditionalHandle h, int use_graph) {
+    if (v.ctr->done) {
+        if (use_graph) cudaGraphSetConditional(h, 0);
+        return;
+    }
+    const int cont = finish_pass(v);
+    if (use_graph) cudaGraphSetConditional(h, cont);
+}
+
+__global__ void k_output(long long C, const long long* __restrict__ Vkey, double* V) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x)
+        V[c] = val_of(Vkey[c]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+static int blocks_for(long long work, int threads) {
+    long long need = (work + threads - 1) / threads;
+    long long cap = (long long)sm_count() * 8;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+template <typename K>
+static int full_wave(K kernel, int threads) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * sm_count();
+}
+
+static int ws_get(const bf_abstraction* a, bf_solve_ws** out) {
+    bf_abstraction* am = const_cast<bf_abstraction*>(a);
+    if (am->ws) { *out = am->ws; return BF_OK; }
+    bf_solve_ws* w = new bf_solve_ws;
+    w->C = a->g.C;
+    w->U = a->g.U;
+    w->D = a->g.D;
+    cudaGetDevice(&w->device);
+    w->nseg_total = (a->g.C + 31) / 32;
+    const long long C = w->C, S = w->nseg_total;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    A((void**)&w->Vkey, 8 * C);
+    A((void**)&w->Vnew, 8 * C);
+    A((void**)&w->mu, C);
+    A((void**)&w->flag, C);
+    A((void**)&w->segflag, 4 * S);
+    A((void**)&w->seglist, 8 * S);
+    A((void**)&w->chg, 4 * C);
+    A((void**)&w->Gint, 8 * C * w->U);
+    A((void**)&w->ctr, sizeof(Counters));
+    if (e != cudaSuccess) { bf_solve_ws_free(w); return bfh::cuda_fail(e, "bf_solve workspace"); }
+    am->ws = w;
+    *out = w;
+    return BF_OK;
+}
+
+static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
+    InstView v;
+    memset(&v, 0, sizeof v);
+    v.g = a->g;
+    v.dd.kind = a->dyn.kind;
+    v.dd.substeps = a->dyn.rk4_substeps;
+    v.dd.udim = a->udim;
+    v.dd.tau = a->tau;
+    for (int i = 0; i < 8; ++i) v.dd.p[i] = a->dyn.param[i];
+    for (int d = 0; d < a->g.D; ++d) {
+        v.dd.glo[d] = a->glo[d];
+        v.dd.eta[d] = (a->ghi[d] - a->glo[d]) / (double)a->g.n[d];
+    }
+    v.boxes = a->d_boxes;
+    v.inputs = a->d_inputs;
+    v.pred = a->d_pred;
+    v.Gint = w->Gint;
+    v.Vkey = w->Vkey;
+    v.Vnew = w->Vnew;
+    v.mu = w->mu;
+    v.flag = w->flag;
+    v.segflag = w->segflag;
+    v.seglist0 = w->seglist;
+    v.seglist1 = w->seglist + w->nseg_total;
+    v.chg = w->chg;
+    v.ctr = w->ctr;
+    v.trace = w->trace;
+    v.trace_cap = w->trace_cap;
+    return v;
+}
+
+// Launch one pass (relax, propagate, finish) of the given dimension.
+template <int D>
+static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
+                        cudaGraphConditionalHandle h, int use_graph) {
+    if (a->mode == BF_MODE_RECOMPUTE) k_relax<D, true><<<w->relax_blocks, 256, 0, st>>>(v);
+    else k_relax<D, false><<<w->relax_blocks, 256, 0, st>>>(v);
+    k_propagate<D><<<w->prop_blocks, 256, 0, st>>>(v, 0);
+    k_finish<<<1, 1, 0, st>>>(v, h, use_graph);
+}
+
+static void launch_pass_any(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
+                            cudaGraphConditionalHandle h, int use_graph) {
+    switch (a->g.D) {
+        case 1: launch_pass<1>(a, w, v, st, h, use_graph); break;
+        case 2: launch_pass<2>(a, w, v, st, h, use_graph); break;
+        case 3: launch_pass<3>(a, w, v, st, h, use_graph); break;
+        default: launch_pass<4>(a, w, v, st, h, use_graph); break;
+    }
+}
+
+static void launch_init_propagate(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st) {
+    switch (a->g.D) {
+        case 1: k_propagate<1><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
+        case 2: k_propagate<2><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
+        case 3: k_propagate<3><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
+        default: k_propagate<4><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
+    }
+}
+
+template <int D>
+static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
+    w->relax_blocks = a->mode == BF_MODE_RECOMPUTE ? full_wave(k_relax<D, true>, 256)
+                                                   : full_wave(k_relax<D, false>, 256);
+    w->prop_blocks = full_wave(k_propagate<D>, 256);
+}
+
+// Build (once per workspace) the graph: [after-init] -> WHILE { pass }.
+static int ws_graph(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
+    if (w->exec) return BF_OK;
+    cudaGraph_t graph;
+    BF_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    BF_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
+    // after-init kernel node
+    cudaGraphNode_t n0;
+    {
+        void* args[] = {(void*)&w->ctr, (void*)&h, nullptr};
+        int use_graph = 1;
+        args[2] = &use_graph;
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void*)k_after_init;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = args;
+        BF_CUDA(cudaGraphAddKernelNode(&n0, graph, nullptr, 0, &kp));
+    }
+    // cudaGraphNodeParams has no usable default constructor: zero raw storage
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t nc;
+    BF_CUDA(cudaGraphAddNode(&nc, graph, &n0, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // capture one pass into the body
+    cudaStream_t cs;
+    BF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    BF_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    InstView v = make_view(a, w);
+    launch_pass_any(a, w, v, cs, h, 1);
+    cudaGraph_t captured;
+    cudaError_t e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    BF_CUDA(e);
+    BF_CUDA(cudaGraphInstantiate(&w->exec, graph, 0));
+    w->graph = graph;
+    (void)st;
+    return BF_OK;
+}
+
+static int stage_in(const void* src, size_t bytes, void** stage, cudaStream_t st, const void** dev) {
+    if (!src) { *dev = nullptr; return BF_OK; }
+    if (bfh::is_device_ptr(src)) { *dev = src; return BF_OK; }
+    if (!*stage) BF_CUDA(cudaMalloc(stage, bytes));
+    BF_CUDA(cudaMemcpyAsync(*stage, src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = *stage;
+    return BF_OK;
+}
+
+extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t* target,
+                        const uint8_t* avoid, const bf_solve_opts* opts, double* V, uint8_t* mu,
+                        int64_t* iters, int32_t* status, void* stream) {
+    if (!a || !G || !V || !mu || !iters || !status) {
+        bfh::set_error("bf_solve: NULL argument");
+        return BF_ERR_INVALID;
+    }
+    const double* terminal = opts ? opts->terminal : nullptr;
+    if (!terminal && !target) {
+        bfh::set_error("bf_solve: need a target mask or a terminal cost");
+        return BF_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    bf_solve_ws* w = nullptr;
+    int rc = ws_get(a, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lock(w->mtx);
+    const long long C = w->C;
+    const int U = w->U;
+    if (!w->relax_blocks) {
+        switch (a->g.D) {
+            case 1: set_blocks<1>(a, w); break;
+            case 2: set_blocks<2>(a, w); break;
+            case 3: set_blocks<3>(a, w); break;
+            default: set_blocks<4>(a, w); break;
+        }
+    }
+    // trace buffer (device side), sized to the request
+    const long long tcap = (opts && opts->trace) ? opts->trace_cap : 0;
+    if (tcap > w->trace_cap) {
+        cudaFree(w->trace);
+        w->trace = nullptr;
+        w->trace_cap = 0;
+        BF_CUDA(cudaMalloc((void**)&w->trace, sizeof(long long) * 4 * tcap));
+        w->trace_cap = tcap;
+        if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+        if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
+    }
+    if (tcap > 0) BF_CUDA(cudaMemsetAsync(w->trace, 0xFF, sizeof(long long) * 4 * w->trace_cap, st));
+    // inputs
+    const void *dG, *dT, *dTgt, *dAv;
+    if ((rc = stage_in(G, sizeof(double) * C * U, (void**)&w->stage_G, st, &dG))) return rc;
+    if ((rc = stage_in(terminal, sizeof(double) * C, (void**)&w->stage_T, st, &dT))) return rc;
+    if ((rc = stage_in(terminal ? nullptr : target, C, (void**)&w->stage_tgt, st, &dTgt))) return rc;
+    if ((rc = stage_in(avoid, C, (void**)&w->stage_avoid, st, &dAv))) return rc;
+    long long cap = C;
+    if (opts && opts->max_iters > 0 && opts->max_iters < cap) cap = opts->max_iters;
+    // set-up: lines 1-10 of Algorithm 1
+    k_init_counters<<<1, 1, 0, st>>>(w->ctr, cap);
+    BF_CUDA(cudaMemsetAsync(w->segflag, 0, 4 * w->nseg_total, st));
+    k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dG, (const unsigned char*)dAv,
+                                                     w->Gint, w->ctr);
+    k_init_values<<<blocks_for(C, 256), 256, 0, st>>>(C, (const double*)dT, (const unsigned char*)dTgt,
+                                                      (const unsigned char*)dAv, w->Vkey, w->Vnew, w->mu,
+                                                      w->flag, w->chg, w->ctr);
+    InstView v = make_view(a, w);
+    launch_init_propagate(a, w, v, st);
+    BF_CUDA(cudaGetLastError());
+    const bool host_loop = opts && (opts->flags & BF_FLAG_HOST_LOOP);
+    if (host_loop) {
+        k_after_init<<<1, 1, 0, st>>>(w->ctr, 0, 0);
+        Counters hc;
+        for (;;) {
+            BF_CUDA(cudaMemcpyAsync(&hc, w->ctr, sizeof hc, cudaMemcpyDeviceToHost, st));
+            BF_CUDA(cudaStreamSynchronize(st));
+            if (hc.done) break;
+            launch_pass_any(a, w, v, st, 0, 0);
+            BF_CUDA(cudaGetLastError());
+        }
+    } else {
+        if ((rc = ws_graph(a, w, st))) return rc;
+        BF_CUDA(cudaGraphLaunch(w->exec, st));
+    }
+    // outputs
+    const bool vdev = bfh::is_device_ptr(V);
+    double* dV = V;
+    if (!vdev) {
+        if (!w->stage_V) BF_CUDA(cudaMalloc((void**)&w->stage_V, 8 * C));
+        dV = w->stage_V;
+    }
+    k_output<<<blocks_for(C, 256), 256, 0, st>>>(C, w->Vkey, dV);
+    BF_CUDA(cudaGetLastError());
+    if (!vdev) BF_CUDA(cudaMemcpyAsync(V, dV, 8 * C, cudaMemcpyDeviceToHost, st));
+    BF_CUDA(cudaMemcpyAsync(mu, w->mu, C, cudaMemcpyDefault, st));
+    Counters hc;
+    BF_CUDA(cudaMemcpyAsync(&hc, w->ctr, sizeof hc, cudaMemcpyDeviceToHost, st));
+    if (tcap > 0)
+        BF_CUDA(cudaMemcpyAsync(opts->trace, w->trace, sizeof(long long) * 4 * tcap, cudaMemcpyDeviceToHost, st));
+    BF_CUDA(cudaStreamSynchronize(st));
+    if (hc.err) {
+        bfh::set_error("bf_solve: NaN, -inf or |value| > 2^64 in G or the terminal cost");
+        return BF_ERR_INVALID;
+    }
+    *iters = hc.round;
+    *status = hc.status;
+    return BF_OK;
+}
