@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the generalized Bellman-Ford solver (arXiv 2001.06231, Alg. 1).
+
+Metric: (cell, input) relaxations per second of Algorithm 1 solving to its
+fixed point.  One step = one bf_solve call (set-up of lines 1-10, every pass
+of the while-loop, output) on the 3-D unicycle workload (200 x 200 x 64 cells
+x 10 inputs, stored boxes) with the abstraction already resident (its build
+is timed separately).  The numerator is the canonical work of Algorithm 1:
+the sum over passes of |F1| x |U| with the exact predecessor sets of Eq.
+(pred), counted once on the device in counting mode (deterministic: passes
+are synchronous).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload unicycle3d|fire4d|di2d]
+
+--impl reference times the CPU oracle (plain single-threaded FP64 C) on a
+bounded sample of the same workload (the first passes of the same solve).
+Under torchrun (N > 1) every rank solves its own replica (the single solve
+does not shard): weak scaling, value = all ranks' relaxations / max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "(cell,input) relaxations/s"
+UNIT = "relaxations/s"
+PROFILE = os.path.join(ROOT, "profiles", "k_relax_unicycle3d_200x200x64.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2001_06231_gb300", "csrc", f)
+                  for f in ("solve_core.cuh", "solve.cu", "bf_internal.cuh", "dynamics.cuh")]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def make_workload(name, rank=0):
+    from paper_2001_06231_gb300 import workloads as wl
+    import math
+    if name == "unicycle3d":
+        w = wl.unicycle3d(seed=wl.SEED_BASE + 2 + 1000 * rank)
+        desc = "unicycle3d 200x200x64 cells x 10 inputs, tau 0.3 s, RK4 8 substeps, 40 obstacles, stored boxes"
+    elif name == "fire4d":
+        w = wl.fire4d(seed=wl.SEED_BASE + 3 + 1000 * rank, tau=2.0,
+                      target=((50.0, 250.0), (50.0, 150.0), (-math.radians(30), math.radians(30)), (10.0, 15.0)))
+        desc = "fire4d 100x100x36x8 cells x 15 inputs, tau 2 s, negative costs over fire, stored boxes"
+    elif name == "di2d":
+        w = wl.di2d()
+        desc = "di2d 64x64 cells x 5 inputs, tau 0.1 s, exact linear flow"
+    else:
+        raise SystemExit("unknown workload " + name)
+    return w, desc
+
+
+def algorithmic_bytes_per_pair(w):
+    # box record (4 * D bytes) + running cost (8 bytes): SURVEY section 8(d)
+    return 4 * w.grid.ndim + 8
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "bf_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and --impl reference)
+# --------------------------------------------------------------------------
+def oracle_sample(w, boxes, budget_s=15.0, passes=None):
+    """Time the oracle on the first passes of the same solve.
+
+    Returns (relaxations/s, sample description, pred build seconds, fn) where
+    fn() re-runs the same timed sample (for repeated reference steps).
+    """
+    import oracle
+    t0 = time.perf_counter()
+    pred = oracle.pred(w.grid.n, w.grid.periodic, boxes)
+    t_pred = time.perf_counter() - t0
+    T = w.terminal()
+
+    def run(m):
+        t = time.perf_counter()
+        r = oracle.solve(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid, max_iters=m, pred_csr=pred)
+        dt = time.perf_counter() - t
+        return int(r["f1"].sum()) * w.ninputs, dt, r["iters"]
+
+    if passes is None:
+        m = 4
+        pairs, dt, it = run(m)
+        while dt < budget_s / 3 and it == m and m < 4096:
+            m *= 2
+            pairs, dt, it = run(m)
+        passes = m
+    else:
+        pairs, dt, it = run(passes)
+    desc = ("first %d passes of the same solve (%d canonical relaxations), oracle single-threaded FP64 C; "
+            "pred index build (%.1f s) not timed" % (passes, pairs, t_pred))
+    return pairs / dt, desc, t_pred, (lambda: run(passes)), passes
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w, desc = make_workload(args.workload)
+    boxes = oracle.build_boxes(w.kind, w.params, w.substeps, w.grid.n, w.grid.lo, w.grid.hi,
+                               w.grid.periodic, w.inputs, w.tau)
+    _, sample, _, fn, passes = oracle_sample(w, boxes, budget_s=6.0)
+    for _ in range(args.warmup):
+        fn()
+    tot_pairs, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        p, dt, _ = fn()
+        tot_pairs += p
+        tot_t += dt
+    value = tot_pairs / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def ours(args, rank, world, local_rank):
+    import torch
+    import paper_2001_06231_gb300 as bf
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    w, desc = make_workload(args.workload, rank)
+    C, U = w.ncells, w.ninputs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A = bf.abs_build_workload(w)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+
+    G = torch.from_numpy(w.G).to(dev)
+    tg = torch.from_numpy(w.target).to(dev)
+    av = torch.from_numpy(w.avoid).to(dev)
+    V = torch.empty(C, dtype=torch.float64, device=dev)
+    mu = torch.empty(C, dtype=torch.uint8, device=dev)
+
+    def solve(**kw):
+        return bf.bf_solve(A, G, target=tg, avoid=av, V=V, mu=mu, stream=stream, **kw)
+
+    # canonical work (exact F1 of Algorithm 1), counted once on the device
+    rc = solve(count_exact=True)
+    canonical = rc["stats"]["exact_f1_cells"] * U
+    executed = rc["stats"]["executed_pairs"]
+    passes = rc["iters"]
+    # relax-kernel time per launch with CUDA events around each launch
+    rt = solve(time_kernels=True)
+    relax_ms_avg = rt["stats"]["relax_ms"] / max(1, rt["stats"]["relax_launches"])
+    prop_ms_avg = rt["stats"]["propagate_ms"] / max(1, rt["stats"]["relax_launches"])
+
+    for _ in range(args.warmup):
+        r = solve()
+    launches = r["stats"]["kernel_launches"]
+    sampler = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r = solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    step_s = ms_max / 1e3 / args.steps
+    value = canonical * world / step_s
+
+    # end to end through the public API with pinned host buffers
+    Gh = torch.from_numpy(w.G).pin_memory()
+    tgh = torch.from_numpy(w.target).pin_memory()
+    avh = torch.from_numpy(w.avoid).pin_memory()
+    Vh = torch.empty(C, dtype=torch.float64).pin_memory()
+    muh = torch.empty(C, dtype=torch.uint8).pin_memory()
+    bf.bf_solve(A, Gh, target=tgh, avoid=avh, V=Vh, mu=muh, stream=stream)
+    ksteps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ksteps):
+        bf.bf_solve(A, Gh, target=tgh, avoid=avh, V=Vh, mu=muh, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ksteps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = canonical * world / e2e_s
+    h2d = w.G.nbytes + w.target.nbytes + w.avoid.nbytes
+    d2h = 8 * C + C
+
+    # roofline of the relax kernel (dominant): algorithmic bytes per launch
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    bpp = algorithmic_bytes_per_pair(w)
+    bytes_per_launch = executed * bpp / max(1, passes)
+    achieved = bytes_per_launch / (relax_ms_avg / 1e3) / 1e9
+    traffic = None
+    if os.path.exists(PROFILE) and args.workload == "unicycle3d":
+        kv = dict(l.split(":", 1) for l in open(PROFILE) if ":" in l and not l.startswith("#"))
+        if kv.get("kernel_hash", "").strip() == kernel_hash():
+            try:
+                traffic = float(kv["traffic_bytes_per_launch"])
+            except (KeyError, ValueError):
+                traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        boxes = A.export_boxes()
+        val, sample, _, _, _ = oracle_sample(w, boxes, budget_s=args.cpu_budget)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "cells": C, "inputs": U, "passes": passes,
+                   "canonical_relaxations_per_step": canonical, "executed_relaxations_per_step": executed,
+                   "l2": "inputs larger than L2 (boxes %d MB + G %d MB > 129 MB)" % (
+                       C * U * 4 * w.grid.ndim >> 20, w.G.nbytes >> 20),
+                   "abs_build_ms": build_s * 1e3, "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_relax",
+                     "peak_source": peak_src, "relax_ms_per_launch": relax_ms_avg,
+                     "propagate_ms_per_launch": prop_ms_avg,
+                     "bytes_per_launch": bytes_per_launch,
+                     "bytes_note": "executed (cell,input) pairs per launch x %d B (box %d B + G 8 B)" % (
+                         bpp, bpp - 8)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+        "gpu_launches": launches * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="unicycle3d", choices=["unicycle3d", "fire4d", "di2d"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

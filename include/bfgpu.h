@@ -165,7 +165,25 @@ BF_API void abs_free(bf_abstraction *abs);
 #define BF_SCHED_SEGMENT 1     /* warp per 32 consecutive cells (lanes = cells) */
 #define BF_SCHED_LIST 2        /* warp per cells in a list (lanes = inputs)     */
 
-#define BF_FLAG_HOST_LOOP 1    /* drive rounds from the host (debugging)        */
+#define BF_FLAG_HOST_LOOP 1    /* drive passes from the host (one sync per pass) */
+#define BF_FLAG_COUNT_EXACT 2  /* also count |F1| of Algorithm 1 with the exact
+                                  pred of Eq. (pred) (extra gather per pair)    */
+#define BF_FLAG_TIME_KERNELS 4 /* host-driven passes with a CUDA event pair
+                                  around every relax and propagate launch       */
+
+/* Statistics of one bf_solve call (all optional outputs). */
+typedef struct {
+    int64_t kernel_launches;   /* kernels of this library the call launched      */
+    int64_t relaxed_cells;     /* sum over passes of cells relaxed (frontier as
+                                  flagged through the predecessor boxes)         */
+    int64_t executed_pairs;    /* relaxed_cells * U                              */
+    int64_t exact_f1_cells;    /* sum over passes of |F1| with exact pred (only
+                                  with BF_FLAG_COUNT_EXACT, else -1)             */
+    int64_t changed_cells;     /* sum over passes of cells whose V decreased    */
+    int64_t relax_launches;    /* relax kernels launched                         */
+    double relax_ms;           /* summed relax kernel time (BF_FLAG_TIME_KERNELS) */
+    double propagate_ms;       /* summed propagate kernel time (same flag)       */
+} bf_solve_stats;
 
 typedef struct {
     int64_t max_iters;         /* 0 -> |X| (the paper's cap); else min(., |X|) */
@@ -173,10 +191,11 @@ typedef struct {
     int32_t flags;             /* BF_FLAG_*                                     */
     const double *terminal;    /* optional [C] terminal cost (host or device);
                                   NULL -> 0 on target cells, +inf elsewhere     */
-    int64_t *trace;            /* optional host [trace_cap][4]: per pass |F1|
-                                  (cells relaxed), changed cells, active
-                                  segments, executed (cell,input) pairs         */
+    int64_t *trace;            /* optional host [trace_cap][4]: per pass cells
+                                  relaxed, cells changed, active segments, and
+                                  exact |F1| (BF_FLAG_COUNT_EXACT, else -1)      */
     int64_t trace_cap;
+    bf_solve_stats *stats;     /* optional output                               */
 } bf_solve_opts;
 
 /* bf_solve -- Algorithm 1 (Sec. IV-A) on the abstraction with running cost G

@@ -28,7 +28,7 @@ BLOCKED = -32768
 LINEAR2D, UNICYCLE3D, FIRE4D = 1, 2, 3
 MODE_STORED, MODE_RECOMPUTE = 0, 1
 SCHED_AUTO, SCHED_SEGMENT, SCHED_LIST = 0, 1, 2
-FLAG_HOST_LOOP = 1
+FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 
 EXPORTED = ["abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
             "abs_free", "bf_solve", "bf_last_error"]
@@ -53,9 +53,20 @@ class Dynamics(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("rk4_substeps", ctypes.c_int32), ("param", ctypes.c_double * 8)]
 
 
+class SolveStats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("relaxed_cells", ctypes.c_int64),
+                ("executed_pairs", ctypes.c_int64), ("exact_f1_cells", ctypes.c_int64),
+                ("changed_cells", ctypes.c_int64), ("relax_launches", ctypes.c_int64),
+                ("relax_ms", ctypes.c_double), ("propagate_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int64), ("schedule", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("terminal", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64)]
+                ("terminal", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
+                ("stats", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -218,8 +229,9 @@ def abs_from_boxes(grid, boxes, stream=None):
 
 
 def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0, schedule=SCHED_AUTO,
-             host_loop=False, trace_cap=0, V=None, mu=None, stream=None):
-    """Algorithm 1 on the device.  Returns dict(V, mu, iters, status[, trace])."""
+             host_loop=False, trace_cap=0, V=None, mu=None, stream=None, count_exact=False,
+             time_kernels=False):
+    """Algorithm 1 on the device.  Returns dict(V, mu, iters, status, stats[, trace])."""
     C = abstraction.ncells
     Gc = _host(G, np.float64)
     tg = _host(target, np.uint8)
@@ -232,8 +244,11 @@ def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0
     opts = SolveOpts()
     opts.max_iters = int(max_iters)
     opts.schedule = int(schedule)
-    opts.flags = FLAG_HOST_LOOP if host_loop else 0
+    opts.flags = ((FLAG_HOST_LOOP if host_loop else 0) | (FLAG_COUNT_EXACT if count_exact else 0)
+                  | (FLAG_TIME_KERNELS if time_kernels else 0))
     opts.terminal = _ptr(tm)
+    stats = SolveStats()
+    opts.stats = ctypes.addressof(stats)
     trace = None
     if trace_cap:
         trace = np.zeros((int(trace_cap), 4), dtype=np.int64)
@@ -243,7 +258,7 @@ def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0
     st = ctypes.c_int32()
     _check(lib().bf_solve(abstraction.handle, _ptr(Gc), _ptr(tg), _ptr(av), ctypes.byref(opts), _ptr(V),
                           _ptr(mu), ctypes.byref(it), ctypes.byref(st), _stream(stream)))
-    out = {"V": V, "mu": mu, "iters": it.value, "status": st.value}
+    out = {"V": V, "mu": mu, "iters": it.value, "status": st.value, "stats": stats.as_dict()}
     if trace is not None:
         k = min(it.value, int(trace_cap))
         out["trace"] = trace[:k].copy()

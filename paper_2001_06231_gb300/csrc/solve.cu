@@ -4,17 +4,17 @@
 // Device state per solve (workspace, cached in the abstraction handle):
 //   Vkey, Vnew  int64 [C]   values as order-preserving keys (bf_internal.cuh)
 //   mu          uint8 [C]
-//   flag        uint8 [C]   cell belongs to the next frontier
-//   segflag     u32 [S]     segment (32 consecutive cells) is in the next list
+//   fbits       u32 [S]     upcoming frontier, one bit per cell; word s covers
+//                           the segment of cells 32s .. 32s+31
 //   seglist     i32 [2][S]  active segments of the current / next frontier
 //   chg         i32 [C]     cells changed in the current pass
 //   Gint        f64 [U][C]  running cost, input-major (coalesced per input),
 //                           +inf on avoid cells; -0 read as +0
-// Frontiers (F1 / F2 of Algorithm 1) are the flag array plus the compacted
-// segment list; rows are never scanned whole.
+// Frontiers (F1 / F2 of Algorithm 1) are the bitmap plus the compacted
+// segment list; the grid is never scanned whole.
 //
 // Round driver: the passes run inside one CUDA graph whose body (relax ->
-// propagate -> finish) sits in a conditional WHILE node; the finishing kernel
+// propagate) sits in a conditional WHILE node; the last block of propagate
 // evaluates "F1 != empty and i < cap" on the device and sets the condition,
 // so a whole solve is one graph launch with no host round trip per pass.
 #include <cstdio>
@@ -36,12 +36,12 @@ struct bf_solve_ws {
     long long* Vkey = nullptr;
     long long* Vnew = nullptr;
     unsigned char* mu = nullptr;
-    unsigned char* flag = nullptr;
-    unsigned* segflag = nullptr;
+    unsigned* fbits = nullptr;
     int* seglist = nullptr;       // 2 * nseg_total
     int* chg = nullptr;
     double* Gint = nullptr;
     Counters* ctr = nullptr;
+    int* stamp = nullptr;           // counting mode only
     // staging for host inputs / outputs
     double* stage_G = nullptr;      // [C][U]
     double* stage_T = nullptr;      // [C]
@@ -61,10 +61,10 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     if (!w) return;
     if (w->exec) cudaGraphExecDestroy(w->exec);
     if (w->graph) cudaGraphDestroy(w->graph);
-    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->mu); cudaFree(w->flag);
-    cudaFree(w->segflag); cudaFree(w->seglist); cudaFree(w->chg); cudaFree(w->Gint);
+    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->mu); cudaFree(w->fbits);
+    cudaFree(w->seglist); cudaFree(w->chg); cudaFree(w->Gint);
     cudaFree(w->ctr); cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt);
-    cudaFree(w->stage_avoid); cudaFree(w->stage_V); cudaFree(w->trace);
+    cudaFree(w->stage_avoid); cudaFree(w->stage_V); cudaFree(w->trace); cudaFree(w->stamp);
     delete w;
 }
 
@@ -105,7 +105,7 @@ __global__ void k_init_costs(long long C, int U, const double* __restrict__ G,
 __global__ void k_init_values(long long C, const double* __restrict__ terminal,
                               const unsigned char* __restrict__ target,
                               const unsigned char* __restrict__ avoid, long long* Vkey,
-                              long long* Vnew, unsigned char* mu, unsigned char* flag, int* chg,
+                              long long* Vnew, unsigned char* mu, int* chg, int* stamp,
                               Counters* ctr) {
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -127,8 +127,8 @@ __global__ void k_init_values(long long C, const double* __restrict__ terminal,
             Vkey[c] = k;
             Vnew[c] = k;
             mu[c] = kHandover;
-            flag[c] = 0;
             finite = k != kKeyInf;
+            if (stamp) stamp[c] = finite ? -1 : -2;   // -1: "changed" before pass 0
         }
         const int slot = warp_append(finite, &ctr->nchg);
         if (finite) chg[slot] = (int)c;
@@ -144,51 +144,63 @@ __global__ void k_init_counters(Counters* ctr, long long cap) {
 // ---------------------------------------------------------------------------
 // pass kernels
 // ---------------------------------------------------------------------------
-template <int D, bool RECOMP>
-__global__ void __launch_bounds__(256) k_relax(InstView v) {
+template <int D, bool RECOMP, bool COUNT>
+__global__ void __launch_bounds__(256, RECOMP ? 2 : 4) k_relax(InstView v) {
     Counters* k = v.ctr;
     if (k->done) return;
-    const int par = (int)(k->round & 1);
+    const long long round = k->round;
+    const int par = (int)(round & 1);
     const int nseg = k->nseg[par];
     const int* list = seglist_of(v, par);
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     long long relaxed = 0;
+    int exact = 0;
     for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < nseg; s += nwarps)
-        relaxed += relax_segment<D, RECOMP>(v, list[s]);
-    if ((threadIdx.x & 31) == 0 && relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
+        relaxed += relax_segment<D, RECOMP, COUNT>(v, list[s], round, &exact);
+    if ((threadIdx.x & 31) == 0) {
+        if (relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
+        if (COUNT && exact) atomicAdd((unsigned long long*)&k->exact, (unsigned long long)exact);
+    }
 }
 
+// Propagate (warp per changed cell).  The last block to finish closes
+// the pass: after the initial propagate it only decides whether to loop;
+// after a pass it runs finish_pass.  With a graph it sets the WHILE
+// condition.
 template <int D>
-__global__ void __launch_bounds__(256) k_propagate(InstView v, int init) {
+__global__ void __launch_bounds__(256, 4) k_propagate(InstView v, int init, cudaGraphConditionalHandle h,
+                                                   int use_graph) {
     Counters* k = v.ctr;
-    if (k->done) return;
+    if (k->done) {
+        if (use_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
+        return;
+    }
     const int par = init ? 0 : (int)((k->round + 1) & 1);
     const int nchg = k->nchg;
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
         propagate_cell<D>(v, v.chg[i], par, !init);
+    if (last_block_done(&k->blocks_done)) {
+        int cont;
+        if (init) {
+            k->nchg = 0;
+            cont = (k->err == 0 && k->nseg[0] > 0 && k->cap > 0) ? 1 : 0;
+            if (!cont) {
+                k->done = 1;
+                k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
+            }
+        } else {
+            cont = finish_pass(v);
+        }
+        if (use_graph) cudaGraphSetConditional(h, cont);
+    }
 }
 
-// After the initial propagate: F1 is in list 0; decide whether to loop.
-__global__ void k_after_init(Counters* k, cudaGraphConditionalHandle h, int use_graph) {
-    k->nchg = 0;
-    int cont = (k->err == 0 && k->nseg[0] > 0 && k->cap > 0) ? 1 : 0;
-    if (!cont) {
-        k->done = 1;
-        k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
-    }
-    if (use_graph) cudaGraphSetConditional(h, cont);
-}
-
-__global__ void k_finish(InstView v, cudaGraphConditionalHandle h, int use_graph) {
-    if (v.ctr->done) {
-        if (use_graph) cudaGraphSetConditional(h, 0);
-        return;
-    }
-    const int cont = finish_pass(v);
-    if (use_graph) cudaGraphSetConditional(h, cont);
+// First node of the graph: copy "not done" into the WHILE condition.
+__global__ void k_loop_cond(Counters* k, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, k->done ? 0 : 1);
 }
 
 __global__ void k_output(long long C, const long long* __restrict__ Vkey, double* V) {
@@ -237,8 +249,7 @@ static int ws_get(const bf_abstraction* a, bf_solve_ws** out) {
     A((void**)&w->Vkey, 8 * C);
     A((void**)&w->Vnew, 8 * C);
     A((void**)&w->mu, C);
-    A((void**)&w->flag, C);
-    A((void**)&w->segflag, 4 * S);
+    A((void**)&w->fbits, 4 * S);
     A((void**)&w->seglist, 8 * S);
     A((void**)&w->chg, 4 * C);
     A((void**)&w->Gint, 8 * C * w->U);
@@ -269,8 +280,7 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.Vkey = w->Vkey;
     v.Vnew = w->Vnew;
     v.mu = w->mu;
-    v.flag = w->flag;
-    v.segflag = w->segflag;
+    v.fbits = w->fbits;
     v.seglist0 = w->seglist;
     v.seglist1 = w->seglist + w->nseg_total;
     v.chg = w->chg;
@@ -280,58 +290,67 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     return v;
 }
 
-// Launch one pass (relax, propagate, finish) of the given dimension.
+// Launch one pass (relax, propagate, finish) of the given dimension.  With
+// timing events, the relax and propagate launches are each bracketed.
+struct PassTimers {
+    cudaEvent_t e[4];
+};
+
 template <int D>
 static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
-                        cudaGraphConditionalHandle h, int use_graph) {
-    if (a->mode == BF_MODE_RECOMPUTE) k_relax<D, true><<<w->relax_blocks, 256, 0, st>>>(v);
-    else k_relax<D, false><<<w->relax_blocks, 256, 0, st>>>(v);
-    k_propagate<D><<<w->prop_blocks, 256, 0, st>>>(v, 0);
-    k_finish<<<1, 1, 0, st>>>(v, h, use_graph);
+                        cudaGraphConditionalHandle h, int use_graph, bool count, PassTimers* tm) {
+    if (tm) cudaEventRecord(tm->e[0], st);
+    const bool rc = a->mode == BF_MODE_RECOMPUTE;
+    if (rc && count) k_relax<D, true, true><<<w->relax_blocks, 256, 0, st>>>(v);
+    else if (rc) k_relax<D, true, false><<<w->relax_blocks, 256, 0, st>>>(v);
+    else if (count) k_relax<D, false, true><<<w->relax_blocks, 256, 0, st>>>(v);
+    else k_relax<D, false, false><<<w->relax_blocks, 256, 0, st>>>(v);
+    if (tm) { cudaEventRecord(tm->e[1], st); cudaEventRecord(tm->e[2], st); }
+    k_propagate<D><<<w->prop_blocks, 256, 0, st>>>(v, 0, h, use_graph);
+    if (tm) cudaEventRecord(tm->e[3], st);
 }
 
 static void launch_pass_any(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
-                            cudaGraphConditionalHandle h, int use_graph) {
+                            cudaGraphConditionalHandle h, int use_graph, bool count = false,
+                            PassTimers* tm = nullptr) {
     switch (a->g.D) {
-        case 1: launch_pass<1>(a, w, v, st, h, use_graph); break;
-        case 2: launch_pass<2>(a, w, v, st, h, use_graph); break;
-        case 3: launch_pass<3>(a, w, v, st, h, use_graph); break;
-        default: launch_pass<4>(a, w, v, st, h, use_graph); break;
+        case 1: launch_pass<1>(a, w, v, st, h, use_graph, count, tm); break;
+        case 2: launch_pass<2>(a, w, v, st, h, use_graph, count, tm); break;
+        case 3: launch_pass<3>(a, w, v, st, h, use_graph, count, tm); break;
+        default: launch_pass<4>(a, w, v, st, h, use_graph, count, tm); break;
     }
 }
 
 static void launch_init_propagate(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st) {
     switch (a->g.D) {
-        case 1: k_propagate<1><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
-        case 2: k_propagate<2><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
-        case 3: k_propagate<3><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
-        default: k_propagate<4><<<w->prop_blocks, 256, 0, st>>>(v, 1); break;
+        case 1: k_propagate<1><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
+        case 2: k_propagate<2><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
+        case 3: k_propagate<3><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
+        default: k_propagate<4><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
     }
 }
 
 template <int D>
 static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
-    w->relax_blocks = a->mode == BF_MODE_RECOMPUTE ? full_wave(k_relax<D, true>, 256)
-                                                   : full_wave(k_relax<D, false>, 256);
+    w->relax_blocks = a->mode == BF_MODE_RECOMPUTE ? full_wave(k_relax<D, true, false>, 256)
+                                                   : full_wave(k_relax<D, false, false>, 256);
     w->prop_blocks = full_wave(k_propagate<D>, 256);
 }
 
-// Build (once per workspace) the graph: [after-init] -> WHILE { pass }.
+// Build (once per workspace) the graph: [loop condition] -> WHILE { pass }.
 static int ws_graph(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
     if (w->exec) return BF_OK;
     cudaGraph_t graph;
     BF_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle h;
     BF_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
-    // after-init kernel node
+    // condition node: loop while the set-up did not already finish the solve
     cudaGraphNode_t n0;
     {
-        void* args[] = {(void*)&w->ctr, (void*)&h, nullptr};
-        int use_graph = 1;
-        args[2] = &use_graph;
+        void* args[] = {(void*)&w->ctr, (void*)&h};
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof kp);
-        kp.func = (void*)k_after_init;
+        kp.func = (void*)k_loop_cond;
         kp.gridDim = dim3(1);
         kp.blockDim = dim3(1);
         kp.kernelParams = args;
@@ -420,28 +439,47 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     if ((rc = stage_in(avoid, C, (void**)&w->stage_avoid, st, &dAv))) return rc;
     long long cap = C;
     if (opts && opts->max_iters > 0 && opts->max_iters < cap) cap = opts->max_iters;
+    const int flags = opts ? opts->flags : 0;
+    const bool count = (flags & BF_FLAG_COUNT_EXACT) != 0;
+    const bool timed = (flags & BF_FLAG_TIME_KERNELS) != 0;
+    const bool host_loop = (flags & BF_FLAG_HOST_LOOP) || count || timed;
+    if (count && !w->stamp) BF_CUDA(cudaMalloc((void**)&w->stamp, sizeof(int) * C));
     // set-up: lines 1-10 of Algorithm 1
     k_init_counters<<<1, 1, 0, st>>>(w->ctr, cap);
-    BF_CUDA(cudaMemsetAsync(w->segflag, 0, 4 * w->nseg_total, st));
+    BF_CUDA(cudaMemsetAsync(w->fbits, 0, 4 * w->nseg_total, st));
     k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dG, (const unsigned char*)dAv,
                                                      w->Gint, w->ctr);
     k_init_values<<<blocks_for(C, 256), 256, 0, st>>>(C, (const double*)dT, (const unsigned char*)dTgt,
                                                       (const unsigned char*)dAv, w->Vkey, w->Vnew, w->mu,
-                                                      w->flag, w->chg, w->ctr);
+                                                      w->chg, count ? w->stamp : nullptr, w->ctr);
     InstView v = make_view(a, w);
+    if (count) v.stamp = w->stamp;
     launch_init_propagate(a, w, v, st);
     BF_CUDA(cudaGetLastError());
-    const bool host_loop = opts && (opts->flags & BF_FLAG_HOST_LOOP);
+    double relax_ms = 0.0, prop_ms = 0.0;
+    long long relax_launches = 0;
     if (host_loop) {
-        k_after_init<<<1, 1, 0, st>>>(w->ctr, 0, 0);
+        PassTimers tm{};
+        if (timed)
+            for (int i = 0; i < 4; ++i) BF_CUDA(cudaEventCreate(&tm.e[i]));
         Counters hc;
         for (;;) {
             BF_CUDA(cudaMemcpyAsync(&hc, w->ctr, sizeof hc, cudaMemcpyDeviceToHost, st));
             BF_CUDA(cudaStreamSynchronize(st));
+            if (timed && relax_launches > 0) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, tm.e[0], tm.e[1]);
+                relax_ms += ms;
+                cudaEventElapsedTime(&ms, tm.e[2], tm.e[3]);
+                prop_ms += ms;
+            }
             if (hc.done) break;
-            launch_pass_any(a, w, v, st, 0, 0);
+            launch_pass_any(a, w, v, st, 0, 0, count, timed ? &tm : nullptr);
+            ++relax_launches;
             BF_CUDA(cudaGetLastError());
         }
+        if (timed)
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(tm.e[i]);
     } else {
         if ((rc = ws_graph(a, w, st))) return rc;
         BF_CUDA(cudaGraphLaunch(w->exec, st));
@@ -468,5 +506,18 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     }
     *iters = hc.round;
     *status = hc.status;
+    if (opts && opts->stats) {
+        bf_solve_stats* o = opts->stats;
+        // set-up: counters, costs, values, first propagate; loop condition
+        // (graph); one relax + propagate per pass; output
+        o->kernel_launches = (host_loop ? 5 : 6) + 2 * hc.round;
+        o->relaxed_cells = hc.total_relaxed;
+        o->executed_pairs = hc.total_relaxed * U;
+        o->exact_f1_cells = count ? hc.total_exact : -1;
+        o->changed_cells = hc.total_changed;
+        o->relax_launches = hc.round;
+        o->relax_ms = timed ? relax_ms : 0.0;
+        o->propagate_ms = timed ? prop_ms : 0.0;
+    }
     return BF_OK;
 }

@@ -25,6 +25,10 @@ Every generator is deterministic in its seed (numpy PCG64).  The recipes:
                  U[0.7,1]) at the cell centre, G = tau (1 - 1.5 I); landing
                  target [50,250] x [50,100] x [-10,10] deg x [10,12.5];
                  6 no-fly boxes (sides U[50,200] m, all psi and V).
+                 At tau = 1 s a 10 m cell moves about one cell per step, so
+                 almost every box keeps its own cell and few cells get a
+                 finite value; the measured 4-D case uses tau = 2 s and the
+                 landing box [50,250] x [50,150] x [-30,30] deg x [10,15].
 * ``batched``    64 unicycle instances, grid scale s ~ logU[1,4],
                  n = (round(50 s), round(50 s), round(16 s)); each with a 1x1
                  target at a random place, 10-40 obstacles and
@@ -211,11 +215,10 @@ def fire_intensity(grid, blobs):
 
 def fire4d(n=(100, 100, 36, 8), seed=SEED_BASE + 3, n_blobs=5, n_nofly=6,
            target=((50.0, 250.0), (50.0, 100.0), (-math.radians(10), math.radians(10)), (10.0, 12.5)),
-           sigma=(10.0, 16.0)):
+           sigma=(10.0, 16.0), tau=1.0):
     rng = np.random.default_rng(seed)
     grid = Grid(tuple(n), (0.0, 0.0, -math.pi, 10.0), (1000.0, 1000.0, math.pi, 20.0),
                 (False, False, True, False))
-    tau = 1.0
     inputs = fire_inputs()
     C, U = grid.ncells, inputs.shape[0]
     blobs = []

@@ -88,7 +88,8 @@ def random_instance(rng, n, periodic, U, reach=2, width=3, neg=True, p_blocked=0
 @pytest.mark.parametrize("n,periodic,U", [
     ([37], [False], 3), ([64], [True], 2),
     ([45, 29], [False, False], 5), ([33, 20], [False, True], 4),
-    ([21, 17, 12], [False, False, True], 6),
+    ([21, 17, 12], [False, False, True], 6), ([20, 9], [True, False], 3),
+    ([70, 5, 6], [True, False, True], 4), ([300], [False], 2),
     ([13, 11, 9, 6], [False, False, True, False], 7),
 ])
 def test_random_abstractions(n, periodic, U):
@@ -96,6 +97,23 @@ def test_random_abstractions(n, periodic, U):
     boxes, G, target, avoid = random_instance(rng, n, periodic, U)
     res, ref = check_parity(n, periodic, boxes, G, target=target, avoid=avoid)
     assert res["iters"] >= 1
+
+
+def test_exact_frontier_count_matches_oracle():
+    """Counting mode reproduces |F1| of Algorithm 1 with the exact pred."""
+    rng = np.random.default_rng(21)
+    n, periodic = [30, 22, 9], [False, False, True]
+    boxes, G, target, avoid = random_instance(rng, n, periodic, 5)
+    A = bf.abs_from_boxes(bf.make_grid(n, [0, 0, 0], [30, 22, 9], periodic), boxes)
+    res = bf.bf_solve(A, G, target=target, avoid=avoid, count_exact=True, trace_cap=4096)
+    T = np.where(target.astype(bool), 0.0, INF)
+    ref = oracle.solve(n, periodic, boxes, G, T, avoid)
+    assert res["iters"] == ref["iters"] and same(res["V"], ref["V"])
+    assert same(res["trace"][:, 3], ref["f1"])
+    assert res["stats"]["exact_f1_cells"] == int(ref["f1"].sum())
+    assert res["stats"]["changed_cells"] == int(ref["changed"].sum())
+    rt = bf.bf_solve(A, G, target=target, avoid=avoid, time_kernels=True)
+    assert same(rt["V"], ref["V"]) and rt["stats"]["relax_ms"] > 0
 
 
 def test_host_loop_equals_graph():
