@@ -212,6 +212,7 @@ def ours(args, rank, world, local_rank):
     mu = torch.empty(C, dtype=torch.uint8, device=dev)
 
     def solve(**kw):
+        kw.setdefault("host_loop", args.host_loop)
         return bf.bf_solve(A, G, target=tg, avoid=av, V=V, mu=mu, stream=stream, **kw)
 
     # canonical work (exact F1 of Algorithm 1), counted once on the device
@@ -337,6 +338,9 @@ def main():
     ap.add_argument("--workload", default="unicycle3d", choices=["unicycle3d", "fire4d", "di2d"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the passes from the host instead of one graph launch per solve "
+                         "(profilers see every pass kernel)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
