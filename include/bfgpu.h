@@ -260,6 +260,40 @@ BF_API void bf_serve_close(bf_server *srv);
 /* bf_last_error -- message of the last failed call on this thread. */
 BF_API const char *bf_last_error(void);
 
+/* bf_solve_noalloc -- the same solve as bf_solve, for callers that must not
+ * have the library allocate device memory.  The paper has no counterpart: it
+ * exists for host programs that hand out all device memory themselves (a
+ * fixed budget carved up at start-up, a memory pool they own, a long-running
+ * loop that may not call cudaMalloc/cudaFree once it runs), where a solver
+ * that allocates its own workspace, or that stages host arrays through
+ * temporary device buffers, cannot be used.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its working
+ * state (values, frontier bitmap and lists, the transposed cost array,
+ * counters) lives in one file-scope device array of BF_NOALLOC_SCRATCH_BYTES
+ * bytes that every GPU which loads the library holds until the process
+ * exits.  An instance needing more than that (about 20 + 8*U bytes per cell
+ * plus small lists) is rejected with BF_ERR_INVALID and a message giving the
+ * size it would need.
+ *
+ * Every array argument must be device memory of the current device (host
+ * pointers are rejected with BF_ERR_INVALID, since copying them would need a
+ * staging buffer): G [C][U], target [C] (ignored when terminal != NULL),
+ * avoid [C] or NULL, terminal [C] or NULL, V [C] and mu [C] as outputs.
+ * iters and status are host pointers.  max_iters as in bf_solve_opts.
+ * Results are identical to bf_solve.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (each call clears what must start at zero), so calls that
+ * may overlap on the GPU -- on different streams, or from different host
+ * threads -- race and must be serialized by the caller. */
+#define BF_NOALLOC_SCRATCH_BYTES (32u << 20)
+BF_API int bf_solve_noalloc(const bf_abstraction *abs, const double *G, const uint8_t *target,
+                            const uint8_t *avoid, const double *terminal, int64_t max_iters,
+                            double *V, uint8_t *mu, int64_t *iters, int32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

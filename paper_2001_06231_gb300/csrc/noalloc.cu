@@ -1,0 +1,311 @@
+// noalloc.cu -- bf_solve_noalloc: the solve of bf_solve for callers that
+// cannot let the library allocate device memory (see bfgpu.h).  The paper has
+// no counterpart to this entry point.
+//
+// All working state lives in g_scratch, a file-scope device array of fixed
+// size.  Host code must not use the name g_scratch as an address (on the host
+// it only stands in for the symbol); the device address is looked up once
+// per device with cudaGetSymbolAddress and passed to the kernels.  The passes
+// are the same device routines as bf_solve (solve_core.cuh), launched from
+// the host in groups of kPassesPerCheck, with one read of the counters per
+// group; kernels launched after the loop condition turned false return at
+// once.
+#include <cstring>
+#include <mutex>
+
+#include <math_constants.h>
+
+#include "solve_core.cuh"
+
+using namespace bfk;
+
+namespace {
+
+constexpr size_t kScratchBytes = BF_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+constexpr int kPassesPerCheck = 8;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mtx;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_scratch on the current device (looked up once).
+int scratch_base(void** out) {
+    int dev = 0;
+    BF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        bfh::set_error("bf_solve_noalloc: device %d out of range", dev);
+        return BF_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_mtx);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return bfh::cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return BF_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Carve the scratch array; returns the bytes needed (may exceed the array).
+struct Layout {
+    size_t ctr, vkey, vnew, fbits, list0, list1, chg, gint, total;
+};
+
+Layout plan(long long C, int U) {
+    const long long S = (C + 31) / 32;
+    Layout L;
+    size_t o = 0;
+    L.ctr = o;   o += round256(sizeof(Counters));
+    L.vkey = o;  o += round256(8 * (size_t)C);
+    L.vnew = o;  o += round256(8 * (size_t)C);
+    L.fbits = o; o += round256(4 * (size_t)S);
+    L.list0 = o; o += round256(4 * (size_t)S);
+    L.list1 = o; o += round256(4 * (size_t)S);
+    L.chg = o;   o += round256(4 * (size_t)C);
+    L.gint = o;  o += round256(8 * (size_t)C * U);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ bool clean_cost(double v, double& out) {
+    if (v != v) return false;
+    if (v == -CUDART_INF) return false;
+    if (v != CUDART_INF && fabs(v) > 18446744073709551616.0) return false;
+    out = (v == 0.0) ? 0.0 : v;
+    return true;
+}
+
+__global__ void k_na_counters(Counters* ctr, long long cap) {
+    memset(ctr, 0, sizeof(Counters));
+    ctr->cap = cap;
+}
+
+__global__ void k_na_costs(long long C, int U, const double* __restrict__ G,
+                           const unsigned char* __restrict__ avoid, double* Gint, Counters* ctr) {
+    bool bad = false;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x) {
+        const bool av = avoid && avoid[c];
+        for (int u = 0; u < U; ++u) {
+            double v;
+            if (!clean_cost(__ldg(G + c * U + u), v)) bad = true;
+            Gint[(long long)u * C + c] = av ? CUDART_INF : v;
+        }
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+__global__ void k_na_values(long long C, const double* __restrict__ terminal,
+                            const unsigned char* __restrict__ target, const unsigned char* __restrict__ avoid,
+                            long long* Vkey, long long* Vnew, unsigned char* mu, int* chg, Counters* ctr) {
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long rounds = (C + stride - 1) / stride;
+    for (long long it = 0; it < rounds; ++it) {
+        const long long c = start + it * stride;
+        bool finite = false;
+        if (c < C) {
+            double t;
+            if (terminal) {
+                if (!clean_cost(terminal[c], t)) { bad = true; t = CUDART_INF; }
+            } else {
+                t = (target && target[c]) ? 0.0 : CUDART_INF;
+            }
+            if (avoid && avoid[c]) t = CUDART_INF;
+            const long long k = key_of(t);
+            Vkey[c] = k;
+            Vnew[c] = k;
+            mu[c] = kHandover;
+            finite = k != kKeyInf;
+        }
+        const int slot = warp_append(finite, &ctr->nchg);
+        if (finite) chg[slot] = (int)c;
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+template <int D, bool RECOMP>
+__global__ void __launch_bounds__(256, RECOMP ? 2 : 4) k_na_relax(InstView v) {
+    Counters* k = v.ctr;
+    if (k->done) return;
+    const long long round = k->round;
+    const int par = (int)(round & 1);
+    const int nseg = k->nseg[par];
+    const int* list = seglist_of(v, par);
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    long long relaxed = 0;
+    int exact = 0;
+    for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < nseg; s += nwarps)
+        relaxed += relax_segment<D, RECOMP, false>(v, list[s], round, &exact);
+    if ((threadIdx.x & 31) == 0 && relaxed)
+        atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256, 4) k_na_propagate(InstView v, int init) {
+    Counters* k = v.ctr;
+    if (k->done) return;
+    const int par = init ? 0 : (int)((k->round + 1) & 1);
+    const int nchg = k->nchg;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
+        propagate_cell<D>(v, v.chg[i], par, !init);
+    if (last_block_done(&k->blocks_done)) {
+        if (init) {
+            k->nchg = 0;
+            const bool cont = k->err == 0 && k->nseg[0] > 0 && k->cap > 0;
+            if (!cont) {
+                k->done = 1;
+                k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
+            }
+        } else {
+            finish_pass(v);
+        }
+    }
+}
+
+__global__ void k_na_output(long long C, const long long* __restrict__ Vkey, double* V) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x)
+        V[c] = val_of(Vkey[c]);
+}
+
+int sms() {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+template <typename K>
+int wave(K kernel) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+    return (per_sm < 1 ? 1 : per_sm) * sms();
+}
+
+template <int D>
+int run(const bf_abstraction* a, const InstView& v, const double* G, const unsigned char* target,
+        const unsigned char* avoid, const double* terminal, double* V, cudaStream_t st,
+        Counters* hc_out) {
+    const long long C = a->g.C;
+    const int U = a->g.U;
+    const bool rc = a->mode == BF_MODE_RECOMPUTE;
+    const int nb = (int)(((C + 255) / 256) < (long long)sms() * 8 ? (C + 255) / 256 : (long long)sms() * 8);
+    const int rb = rc ? wave(k_na_relax<D, true>) : wave(k_na_relax<D, false>);
+    const int pb = wave(k_na_propagate<D>);
+    k_na_costs<<<nb, 256, 0, st>>>(C, U, G, avoid, const_cast<double*>(v.Gint), v.ctr);
+    k_na_values<<<nb, 256, 0, st>>>(C, terminal, terminal ? nullptr : target, avoid, v.Vkey, v.Vnew, v.mu,
+                                    v.chg, v.ctr);
+    k_na_propagate<D><<<pb, 256, 0, st>>>(v, 1);
+    BF_CUDA(cudaGetLastError());
+    Counters hc;
+    for (;;) {
+        BF_CUDA(cudaMemcpyAsync(&hc, v.ctr, sizeof hc, cudaMemcpyDeviceToHost, st));
+        BF_CUDA(cudaStreamSynchronize(st));
+        if (hc.done) break;
+        for (int i = 0; i < kPassesPerCheck; ++i) {
+            if (rc) k_na_relax<D, true><<<rb, 256, 0, st>>>(v);
+            else k_na_relax<D, false><<<rb, 256, 0, st>>>(v);
+            k_na_propagate<D><<<pb, 256, 0, st>>>(v, 0);
+        }
+        BF_CUDA(cudaGetLastError());
+    }
+    k_na_output<<<nb, 256, 0, st>>>(C, v.Vkey, V);
+    BF_CUDA(cudaGetLastError());
+    BF_CUDA(cudaStreamSynchronize(st));
+    *hc_out = hc;
+    return BF_OK;
+}
+
+bool on_device(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int bf_solve_noalloc(const bf_abstraction* a, const double* G, const uint8_t* target,
+                                const uint8_t* avoid, const double* terminal, int64_t max_iters,
+                                double* V, uint8_t* mu, int64_t* iters, int32_t* status, void* stream) {
+    if (!a || !G || !V || !mu || !iters || !status || (!target && !terminal)) {
+        bfh::set_error("bf_solve_noalloc: NULL argument (need G, V, mu, iters, status and target or terminal)");
+        return BF_ERR_INVALID;
+    }
+    if (!on_device(G) || !on_device(target) || !on_device(avoid) || !on_device(terminal) ||
+        !on_device(V) || !on_device(mu)) {
+        bfh::set_error("bf_solve_noalloc: every array must be device memory of the current device "
+                       "(it does not stage host arrays)");
+        return BF_ERR_INVALID;
+    }
+    const long long C = a->g.C;
+    const int U = a->g.U;
+    const Layout L = plan(C, U);
+    if (L.total > kScratchBytes) {
+        bfh::set_error("bf_solve_noalloc: %lld cells x %d inputs need %zu bytes of scratch, more than the "
+                       "%zu bytes this entry point holds; use bf_solve", C, U, L.total, kScratchBytes);
+        return BF_ERR_INVALID;
+    }
+    void* base = nullptr;
+    int rc = scratch_base(&base);
+    if (rc) return rc;
+    unsigned char* s = static_cast<unsigned char*>(base);
+    cudaStream_t st = (cudaStream_t)stream;
+    InstView v;
+    memset(&v, 0, sizeof v);
+    v.g = a->g;
+    v.dd.kind = a->dyn.kind;
+    v.dd.substeps = a->dyn.rk4_substeps;
+    v.dd.udim = a->udim;
+    v.dd.tau = a->tau;
+    for (int i = 0; i < 8; ++i) v.dd.p[i] = a->dyn.param[i];
+    for (int d = 0; d < a->g.D; ++d) {
+        v.dd.glo[d] = a->glo[d];
+        v.dd.eta[d] = (a->ghi[d] - a->glo[d]) / (double)a->g.n[d];
+    }
+    v.boxes = a->d_boxes;
+    v.inputs = a->d_inputs;
+    v.pred = a->d_pred;
+    v.Gint = reinterpret_cast<const double*>(s + L.gint);
+    v.Vkey = reinterpret_cast<long long*>(s + L.vkey);
+    v.Vnew = reinterpret_cast<long long*>(s + L.vnew);
+    v.mu = mu;
+    v.fbits = reinterpret_cast<unsigned*>(s + L.fbits);
+    v.seglist0 = reinterpret_cast<int*>(s + L.list0);
+    v.seglist1 = reinterpret_cast<int*>(s + L.list1);
+    v.chg = reinterpret_cast<int*>(s + L.chg);
+    v.ctr = reinterpret_cast<Counters*>(s + L.ctr);
+    long long cap = C;
+    if (max_iters > 0 && max_iters < cap) cap = max_iters;
+    // what must start at zero: the counters and the frontier bitmap
+    k_na_counters<<<1, 1, 0, st>>>(v.ctr, cap);
+    BF_CUDA(cudaMemsetAsync(v.fbits, 0, 4 * (size_t)((C + 31) / 32), st));
+    Counters hc;
+    switch (a->g.D) {
+        case 1: rc = run<1>(a, v, G, target, avoid, terminal, V, st, &hc); break;
+        case 2: rc = run<2>(a, v, G, target, avoid, terminal, V, st, &hc); break;
+        case 3: rc = run<3>(a, v, G, target, avoid, terminal, V, st, &hc); break;
+        default: rc = run<4>(a, v, G, target, avoid, terminal, V, st, &hc); break;
+    }
+    if (rc) return rc;
+    if (hc.err) {
+        bfh::set_error("bf_solve_noalloc: NaN, -inf or |value| > 2^64 in G or the terminal cost");
+        return BF_ERR_INVALID;
+    }
+    *iters = hc.round;
+    *status = hc.status;
+    return BF_OK;
+}
