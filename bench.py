@@ -329,13 +329,82 @@ def ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# batched form: 64 unicycle instances on uneven grids, one bf_solve_batch per step
+# --------------------------------------------------------------------------
+def batched(args):
+    import torch
+    import paper_2001_06231_gb300 as bf
+    from paper_2001_06231_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ws = wl.batched(count=args.batch)
+    t0 = time.perf_counter()
+    As = [bf.abs_build_workload(w) for w in ws]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Gs = [torch.from_numpy(w.G).cuda() for w in ws]
+    tgs = [torch.from_numpy(w.target).cuda() for w in ws]
+    avs = [torch.from_numpy(w.avoid).cuda() for w in ws]
+    Vs = [torch.empty(w.ncells, dtype=torch.float64, device="cuda") for w in ws]
+    mus = [torch.empty(w.ncells, dtype=torch.uint8, device="cuda") for w in ws]
+    canonical, executed, passes = 0, 0, []
+    for A, w, G, tg, av, V, mu in zip(As, ws, Gs, tgs, avs, Vs, mus):
+        r = bf.bf_solve(A, G, target=tg, avoid=av, V=V, mu=mu, count_exact=True, stream=stream)
+        canonical += r["stats"]["exact_f1_cells"] * w.ninputs
+        executed += r["stats"]["executed_pairs"]
+        passes.append(r["iters"])
+
+    def batch_step():
+        return bf.bf_solve_batch(As, Gs, targets=tgs, avoids=avs, Vs=Vs, mus=mus, stream=stream)
+
+    def seq_step():
+        for A, G, tg, av, V, mu in zip(As, Gs, tgs, avs, Vs, mus):
+            bf.bf_solve(A, G, target=tg, avoid=av, V=V, mu=mu, stream=stream)
+
+    for _ in range(args.warmup):
+        batch_step()
+        seq_step()
+    sampler = ClockSampler(0)
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    batch_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    e0.record(stream)
+    for _ in range(args.steps):
+        seq_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    n = len(ws)
+    line = {"metric": METRIC, "value": canonical / batch_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": batch_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched: %d unicycle3d instances, grids logU 50x50x16..200x200x64, own "
+                                   "targets/obstacles/costs, one bf_solve_batch per step" % n,
+                       "cells": int(sum(w.ncells for w in ws)), "passes_max": max(passes),
+                       "passes_mean": sum(passes) / n, "canonical_relaxations_per_step": canonical,
+                       "executed_relaxations_per_step": executed, "abs_build_ms": build_s * 1e3},
+            "queries_per_s": n / batch_s, "sequential_queries_per_s": n / seq_s,
+            "sequential_ms_per_step": seq_s * 1e3, "batched_over_sequential": seq_s / batch_s,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="unicycle3d", choices=["unicycle3d", "fire4d", "di2d"])
+    ap.add_argument("--workload", default="unicycle3d", choices=["unicycle3d", "fire4d", "di2d", "batched"])
+    ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--host-loop", action="store_true",
@@ -347,6 +416,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+    elif args.workload == "batched":
+        batched(args)
     else:
         ours(args, rank, world, local_rank)
 

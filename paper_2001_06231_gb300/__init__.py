@@ -31,7 +31,7 @@ SCHED_AUTO, SCHED_SEGMENT, SCHED_LIST = 0, 1, 2
 FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 
 EXPORTED = ["abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
-            "abs_free", "bf_solve", "bf_last_error"]
+            "abs_free", "bf_solve", "bf_solve_batch", "bf_last_error"]
 
 
 class BfError(RuntimeError):
@@ -104,9 +104,10 @@ def lib():
         L.abs_free.argtypes = [P]
         L.abs_free.restype = None
         L.bf_solve.argtypes = [P, P, P, P, P, P, P, P, P, P]
+        L.bf_solve_batch.argtypes = [i32, P, P, P, P, P, i64, P, P, P, P, P]
         L.bf_last_error.restype = ctypes.c_char_p
         for name in ("abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
-                     "bf_solve"):
+                     "bf_solve", "bf_solve_batch"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -263,3 +264,35 @@ def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0
         k = min(it.value, int(trace_cap))
         out["trace"] = trace[:k].copy()
     return out
+
+
+def _ptr_array(items, conv):
+    arr = (ctypes.c_void_p * len(items))()
+    keep = []
+    for i, a in enumerate(items):
+        a = conv(a)
+        keep.append(a)
+        arr[i] = _ptr(a)
+    return arr, keep
+
+
+def bf_solve_batch(abstractions, Gs, targets=None, avoids=None, terminals=None, max_iters=0, Vs=None,
+                   mus=None, stream=None):
+    """Solve many instances together (bf_solve_batch).  Returns a list of dicts."""
+    n = len(abstractions)
+    if Vs is None:
+        Vs = [np.empty(a.ncells, dtype=np.float64) for a in abstractions]
+    if mus is None:
+        mus = [np.empty(a.ncells, dtype=np.uint8) for a in abstractions]
+    absa = (ctypes.c_void_p * n)(*[a.handle.value for a in abstractions])
+    ga, k1 = _ptr_array(Gs, lambda a: _host(a, np.float64))
+    ta, k2 = _ptr_array(targets if targets is not None else [None] * n, lambda a: _host(a, np.uint8))
+    va, k3 = _ptr_array(avoids if avoids is not None else [None] * n, lambda a: _host(a, np.uint8))
+    tm, k4 = _ptr_array(terminals if terminals is not None else [None] * n, lambda a: _host(a, np.float64))
+    Va, k5 = _ptr_array(Vs, lambda a: a)
+    ma, k6 = _ptr_array(mus, lambda a: a)
+    it = (ctypes.c_int64 * n)()
+    st = (ctypes.c_int32 * n)()
+    _check(lib().bf_solve_batch(n, absa, ga, ta, va, tm if terminals is not None else None, int(max_iters),
+                                Va, ma, it, st, _stream(stream)))
+    return [{"V": Vs[i], "mu": mus[i], "iters": it[i], "status": st[i]} for i in range(n)]

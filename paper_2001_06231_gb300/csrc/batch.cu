@@ -1,0 +1,562 @@
+// batch.cu -- bf_solve_batch and the batched pass engine (batch_engine.cuh).
+//
+// Work distribution: after each phase a one-block planning kernel turns the
+// per-instance work counts (segments of the current frontier, or changed
+// cells) into an exclusive prefix over the instance list, ordered by group.
+// A relax (or propagate) launch for group g then has scan[gend] - scan[gbeg]
+// work items; warp w takes item k, finds its instance by binary search over
+// the prefix and runs the same per-warp routine as the single solve.  The
+// planning kernel after propagate also closes the pass of every unfinished
+// instance (finish_pass) and counts the instances still running.
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "batch_engine.cuh"
+
+using namespace bfk;
+
+namespace bfb {
+
+// ---------------------------------------------------------------------------
+// set-up kernels (one instance at a time)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool b_clean(double v, double& out) {
+    if (v != v) return false;
+    if (v == -CUDART_INF) return false;
+    if (v != CUDART_INF && fabs(v) > 18446744073709551616.0) return false;
+    out = (v == 0.0) ? 0.0 : v;
+    return true;
+}
+
+__global__ void k_b_counters(Counters* ctr, long long cap) {
+    memset(ctr, 0, sizeof(Counters));
+    ctr->cap = cap;
+}
+
+__global__ void k_b_costs(long long C, int U, const double* __restrict__ G,
+                          const unsigned char* __restrict__ avoid, double* Gint, Counters* ctr) {
+    bool bad = false;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x) {
+        const bool av = avoid && avoid[c];
+        for (int u = 0; u < U; ++u) {
+            double v;
+            if (!b_clean(__ldg(G + c * U + u), v)) bad = true;
+            Gint[(long long)u * C + c] = av ? CUDART_INF : v;
+        }
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+__global__ void k_b_values(long long C, const double* __restrict__ terminal,
+                           const unsigned char* __restrict__ target, const unsigned char* __restrict__ avoid,
+                           long long* Vkey, long long* Vnew, unsigned char* mu, int* chg, Counters* ctr) {
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long rounds = (C + stride - 1) / stride;
+    for (long long it = 0; it < rounds; ++it) {
+        const long long c = start + it * stride;
+        bool finite = false;
+        if (c < C) {
+            double t;
+            if (terminal) {
+                if (!b_clean(terminal[c], t)) { bad = true; t = CUDART_INF; }
+            } else {
+                t = (target && target[c]) ? 0.0 : CUDART_INF;
+            }
+            if (avoid && avoid[c]) t = CUDART_INF;
+            const long long k = key_of(t);
+            Vkey[c] = k;
+            Vnew[c] = k;
+            mu[c] = kHandover;
+            finite = k != kKeyInf;
+        }
+        const int slot = warp_append(finite, &ctr->nchg);
+        if (finite) chg[slot] = (int)c;
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256, 4) k_b_propagate_init(InstView v) {
+    const int nchg = v.ctr->nchg;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
+        propagate_cell<D>(v, v.chg[i], 0, false);
+}
+
+__global__ void k_b_output(long long C, const long long* __restrict__ Vkey, double* V) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x)
+        V[c] = val_of(Vkey[c]);
+}
+
+// ---------------------------------------------------------------------------
+// batched pass kernels
+// ---------------------------------------------------------------------------
+
+// Largest i in [beg, end) with scan[i] <= pos.
+__device__ __forceinline__ int find_instance(const int* __restrict__ scan, int beg, int end, int pos) {
+    int lo = beg, hi = end - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (scan[mid] <= pos) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Planning (one block of 1024 threads).
+//   mode 0 (after set-up): decide which instances start looping; work = segments.
+//   mode 1 (after relax):  work = changed cells.
+//   mode 2 (after propagate): close the pass of each unfinished instance; work = segments.
+// Writes scan[0..n], totals per group and, in modes 0 and 2, the number of
+// unfinished instances (and the WHILE condition of the graph).
+__global__ void __launch_bounds__(1024) k_b_plan(BatchDev b, int mode, cudaGraphConditionalHandle h,
+                                                 int use_graph) {
+    __shared__ int sums[1024];
+    __shared__ int active;
+    const int t = threadIdx.x, bd = blockDim.x;
+    if (t == 0) active = 0;
+    __syncthreads();
+    const int n = b.n;
+    const int chunk = (n + bd - 1) / bd;
+    const int i0 = min(n, t * chunk), i1 = min(n, i0 + chunk);
+    int local = 0, alive = 0;
+    for (int i = i0; i < i1; ++i) {
+        const InstView& v = b.views[i];
+        Counters* k = v.ctr;
+        int cnt = 0;
+        if (!k->done) {
+            if (mode == 0) {
+                k->nchg = 0;
+                const bool cont = k->err == 0 && k->nseg[0] > 0 && k->cap > 0;
+                if (!cont) {
+                    k->done = 1;
+                    k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
+                } else {
+                    cnt = k->nseg[0];
+                }
+            } else if (mode == 1) {
+                cnt = k->nchg;
+            } else {
+                if (finish_pass(v)) cnt = k->nseg[k->round & 1];
+            }
+            if (!k->done) ++alive;
+        }
+        b.scan[i] = cnt;
+        local += cnt;
+    }
+    if (alive) atomicAdd(&active, alive);
+    sums[t] = local;
+    __syncthreads();
+    // inclusive scan of the per-thread sums (Hillis-Steele)
+    for (int off = 1; off < bd; off <<= 1) {
+        const int x = t >= off ? sums[t - off] : 0;
+        __syncthreads();
+        sums[t] += x;
+        __syncthreads();
+    }
+    int run = t > 0 ? sums[t - 1] : 0;
+    for (int i = i0; i < i1; ++i) {
+        const int c = b.scan[i];
+        b.scan[i] = run;
+        run += c;
+    }
+    __syncthreads();
+    if (t == 0) {
+        b.scan[n] = sums[bd - 1];
+        for (int g = 0; g < b.ngroups; ++g) b.totals[g] = 0;   // totals are read from scan
+        if (mode != 1) {
+            *b.active = active;
+            if (use_graph) cudaGraphSetConditional(h, active > 0 ? 1 : 0);
+        }
+    }
+}
+
+__global__ void k_b_cond(const int* active, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, *active > 0 ? 1 : 0);
+}
+
+template <int D, bool RECOMP>
+__global__ void __launch_bounds__(256, RECOMP ? 2 : 4) k_b_relax(BatchDev b, int g) {
+    const int beg = b.gbeg[g], end = b.gbeg[g + 1];
+    if (beg >= end) return;
+    const int base = b.scan[beg], total = b.scan[end] - base;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < total; item += nwarps) {
+        const int pos = base + item;
+        const int i = find_instance(b.scan, beg, end, pos);
+        const InstView& v = b.views[i];
+        const long long round = v.ctr->round;
+        const int seg = seglist_of(v, (int)(round & 1))[pos - b.scan[i]];
+        int exact = 0;
+        const int r = relax_segment<D, RECOMP, false>(v, seg, round, &exact);
+        if ((threadIdx.x & 31) == 0 && r)
+            atomicAdd((unsigned long long*)&v.ctr->relaxed, (unsigned long long)r);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256, 4) k_b_propagate(BatchDev b, int g) {
+    const int beg = b.gbeg[g], end = b.gbeg[g + 1];
+    if (beg >= end) return;
+    const int base = b.scan[beg], total = b.scan[end] - base;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < total; item += nwarps) {
+        const int pos = base + item;
+        const int i = find_instance(b.scan, beg, end, pos);
+        const InstView& v = b.views[i];
+        const int par = (int)((v.ctr->round + 1) & 1);
+        propagate_cell<D>(v, v.chg[pos - b.scan[i]], par, true);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+static int n_sms() {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+static int blocks_for(long long work) {
+    long long need = (work + 255) / 256;
+    const long long cap = (long long)n_sms() * 8;
+    return (int)std::max(1LL, std::min(need, cap));
+}
+
+static size_t r256(size_t b) { return (b + 255) & ~size_t(255); }
+
+Engine::~Engine() {
+    for (InstState* s : insts_) {
+        cudaFreeAsync(s->mem, st_);
+        delete s;
+    }
+    insts_.clear();
+    if (dev_mem_) cudaFreeAsync(dev_mem_, st_);
+    cudaStreamSynchronize(st_);
+}
+
+static int group_of(const bf_abstraction* a) {
+    return (a->g.D - 1) * 2 + (a->mode == BF_MODE_RECOMPUTE ? 1 : 0);
+}
+
+int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* target,
+                const unsigned char* avoid, const double* terminal, long long max_iters, double* V,
+                unsigned char* mu, InstState** out) {
+    if (!a || !G || !V || !mu || (!target && !terminal)) {
+        bfh::set_error("batch: instance needs an abstraction, G, V, mu and a target or terminal cost");
+        return BF_ERR_INVALID;
+    }
+    const long long C = a->g.C;
+    const int U = a->g.U;
+    const long long S = (C + 31) / 32;
+    const bool sG = !bfh::is_device_ptr(G);
+    const bool sT = terminal && !bfh::is_device_ptr(terminal);
+    const bool sTg = !terminal && target && !bfh::is_device_ptr(target);
+    const bool sAv = avoid && !bfh::is_device_ptr(avoid);
+    const bool vdev = bfh::is_device_ptr(V);
+    const bool mdev = bfh::is_device_ptr(mu);
+    size_t o = 0;
+    const size_t o_ctr = o;  o += r256(sizeof(Counters));
+    const size_t o_vk = o;   o += r256(8 * (size_t)C);
+    const size_t o_vn = o;   o += r256(8 * (size_t)C);
+    const size_t o_mu = o;   o += r256((size_t)C);
+    const size_t o_fb = o;   o += r256(4 * (size_t)S);
+    const size_t o_l0 = o;   o += r256(4 * (size_t)S);
+    const size_t o_l1 = o;   o += r256(4 * (size_t)S);
+    const size_t o_chg = o;  o += r256(4 * (size_t)C);
+    const size_t o_gi = o;   o += r256(8 * (size_t)C * U);
+    const size_t o_sg = o;   o += sG ? r256(8 * (size_t)C * U) : 0;
+    const size_t o_st = o;   o += sT ? r256(8 * (size_t)C) : 0;
+    const size_t o_stg = o;  o += sTg ? r256((size_t)C) : 0;
+    const size_t o_sav = o;  o += sAv ? r256((size_t)C) : 0;
+    const size_t o_sv = o;   o += vdev ? 0 : r256(8 * (size_t)C);
+    void* mem = nullptr;
+    BF_CUDA(cudaMallocAsync(&mem, o, st_));
+    unsigned char* m = static_cast<unsigned char*>(mem);
+    InstState* s = new InstState;
+    s->a = a;
+    s->mem = mem;
+    s->group = group_of(a);
+    s->cap = (max_iters > 0 && max_iters < C) ? max_iters : C;
+    InstView& v = s->view;
+    memset(&v, 0, sizeof v);
+    v.g = a->g;
+    v.dd.kind = a->dyn.kind;
+    v.dd.substeps = a->dyn.rk4_substeps;
+    v.dd.udim = a->udim;
+    v.dd.tau = a->tau;
+    for (int i = 0; i < 8; ++i) v.dd.p[i] = a->dyn.param[i];
+    for (int d = 0; d < a->g.D; ++d) {
+        v.dd.glo[d] = a->glo[d];
+        v.dd.eta[d] = (a->ghi[d] - a->glo[d]) / (double)a->g.n[d];
+    }
+    v.boxes = a->d_boxes;
+    v.inputs = a->d_inputs;
+    v.pred = a->d_pred;
+    v.ctr = reinterpret_cast<Counters*>(m + o_ctr);
+    v.Vkey = reinterpret_cast<long long*>(m + o_vk);
+    v.Vnew = reinterpret_cast<long long*>(m + o_vn);
+    v.mu = m + o_mu;
+    v.fbits = reinterpret_cast<unsigned*>(m + o_fb);
+    v.seglist0 = reinterpret_cast<int*>(m + o_l0);
+    v.seglist1 = reinterpret_cast<int*>(m + o_l1);
+    v.chg = reinterpret_cast<int*>(m + o_chg);
+    v.Gint = reinterpret_cast<const double*>(m + o_gi);
+    // inputs
+    const double* dG = G;
+    if (sG) {
+        BF_CUDA(cudaMemcpyAsync(m + o_sg, G, 8 * (size_t)C * U, cudaMemcpyHostToDevice, st_));
+        dG = reinterpret_cast<const double*>(m + o_sg);
+    }
+    const double* dT = terminal;
+    if (sT) {
+        BF_CUDA(cudaMemcpyAsync(m + o_st, terminal, 8 * (size_t)C, cudaMemcpyHostToDevice, st_));
+        dT = reinterpret_cast<const double*>(m + o_st);
+    }
+    const unsigned char* dTg = terminal ? nullptr : target;
+    if (sTg) {
+        BF_CUDA(cudaMemcpyAsync(m + o_stg, target, (size_t)C, cudaMemcpyHostToDevice, st_));
+        dTg = m + o_stg;
+    }
+    const unsigned char* dAv = avoid;
+    if (sAv) {
+        BF_CUDA(cudaMemcpyAsync(m + o_sav, avoid, (size_t)C, cudaMemcpyHostToDevice, st_));
+        dAv = m + o_sav;
+    }
+    s->Vdev = vdev ? V : reinterpret_cast<double*>(m + o_sv);
+    s->V_host = vdev ? nullptr : V;
+    s->mu_host = mdev ? nullptr : mu;
+    s->mu_dev_out = mdev ? mu : nullptr;
+    // lines 1-10 of Algorithm 1
+    k_b_counters<<<1, 1, 0, st_>>>(v.ctr, s->cap);
+    BF_CUDA(cudaMemsetAsync(v.fbits, 0, 4 * (size_t)S, st_));
+    const int nb = blocks_for(C);
+    k_b_costs<<<nb, 256, 0, st_>>>(C, U, dG, dAv, const_cast<double*>(v.Gint), v.ctr);
+    k_b_values<<<nb, 256, 0, st_>>>(C, dT, dTg, dAv, v.Vkey, v.Vnew, v.mu, v.chg, v.ctr);
+    const int pb = n_sms() * 4;
+    switch (a->g.D) {
+        case 1: k_b_propagate_init<1><<<pb, 256, 0, st_>>>(v); break;
+        case 2: k_b_propagate_init<2><<<pb, 256, 0, st_>>>(v); break;
+        case 3: k_b_propagate_init<3><<<pb, 256, 0, st_>>>(v); break;
+        default: k_b_propagate_init<4><<<pb, 256, 0, st_>>>(v); break;
+    }
+    BF_CUDA(cudaGetLastError());
+    insts_.push_back(s);
+    if (out) *out = s;
+    return BF_OK;
+}
+
+void Engine::remove(InstState* s) {
+    auto it = std::find(insts_.begin(), insts_.end(), s);
+    if (it != insts_.end()) insts_.erase(it);
+    cudaFreeAsync(s->mem, st_);
+    delete s;
+}
+
+int Engine::rebuild() {
+    std::stable_sort(insts_.begin(), insts_.end(),
+                     [](const InstState* x, const InstState* y) { return x->group < y->group; });
+    const int n = (int)insts_.size();
+    memset(&dev_, 0, sizeof dev_);
+    dev_.n = n;
+    // groups
+    int ng = 0;
+    for (int i = 0; i < n; ++i) {
+        const int g = insts_[i]->group;
+        if (ng == 0 || group_D_[ng - 1] * 2 + group_rc_[ng - 1] - 2 != g) {
+            group_D_[ng] = g / 2 + 1;
+            group_rc_[ng] = g % 2;
+            dev_.gbeg[ng] = i;
+            ++ng;
+        }
+    }
+    dev_.ngroups = ng;
+    dev_.gbeg[ng] = n;
+    const size_t need = r256(sizeof(InstView) * std::max(n, 1)) + r256(4 * (size_t)(n + 1)) +
+                        r256(4 * kMaxGroups) + r256(4);
+    if (need > dev_mem_bytes_) {
+        if (dev_mem_) BF_CUDA(cudaFreeAsync(dev_mem_, st_));
+        dev_mem_ = nullptr;
+        BF_CUDA(cudaMallocAsync(&dev_mem_, need, st_));
+        dev_mem_bytes_ = need;
+    }
+    unsigned char* m = static_cast<unsigned char*>(dev_mem_);
+    dev_.views = reinterpret_cast<InstView*>(m);
+    m += r256(sizeof(InstView) * std::max(n, 1));
+    dev_.scan = reinterpret_cast<int*>(m);
+    m += r256(4 * (size_t)(n + 1));
+    dev_.totals = reinterpret_cast<int*>(m);
+    m += r256(4 * kMaxGroups);
+    dev_.active = reinterpret_cast<int*>(m);
+    std::vector<InstView> hv(n);
+    for (int i = 0; i < n; ++i) hv[i] = insts_[i]->view;
+    if (n) BF_CUDA(cudaMemcpyAsync(dev_.views, hv.data(), sizeof(InstView) * n, cudaMemcpyHostToDevice, st_));
+    if (!relax_blocks_) {
+        relax_blocks_ = n_sms() * 4;
+        prop_blocks_ = n_sms() * 4;
+    }
+    return BF_OK;
+}
+
+template <int D>
+static void launch_relax(const BatchDev& b, int g, int rc, int blocks, cudaStream_t st) {
+    if (rc) k_b_relax<D, true><<<blocks / 2, 256, 0, st>>>(b, g);
+    else k_b_relax<D, false><<<blocks, 256, 0, st>>>(b, g);
+}
+
+template <int D>
+static void launch_prop(const BatchDev& b, int g, int blocks, cudaStream_t st) {
+    k_b_propagate<D><<<blocks, 256, 0, st>>>(b, g);
+}
+
+void Engine::launch_pass(cudaGraphConditionalHandle h, int use_graph) {
+    for (int g = 0; g < dev_.ngroups; ++g) {
+        switch (group_D_[g]) {
+            case 1: launch_relax<1>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
+            case 2: launch_relax<2>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
+            case 3: launch_relax<3>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
+            default: launch_relax<4>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
+        }
+    }
+    k_b_plan<<<1, 1024, 0, st_>>>(dev_, 1, h, use_graph);
+    for (int g = 0; g < dev_.ngroups; ++g) {
+        switch (group_D_[g]) {
+            case 1: launch_prop<1>(dev_, g, prop_blocks_, st_); break;
+            case 2: launch_prop<2>(dev_, g, prop_blocks_, st_); break;
+            case 3: launch_prop<3>(dev_, g, prop_blocks_, st_); break;
+            default: launch_prop<4>(dev_, g, prop_blocks_, st_); break;
+        }
+    }
+    k_b_plan<<<1, 1024, 0, st_>>>(dev_, 2, h, use_graph);
+}
+
+int Engine::run_to_completion() {
+    if (dev_.n == 0) return BF_OK;
+    k_b_plan<<<1, 1024, 0, st_>>>(dev_, 0, 0, 0);
+    BF_CUDA(cudaGetLastError());
+    cudaGraph_t graph;
+    BF_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    BF_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault));
+    cudaGraphNode_t n0;
+    {
+        void* args[] = {(void*)&dev_.active, (void*)&h};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void*)k_b_cond;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = args;
+        BF_CUDA(cudaGraphAddKernelNode(&n0, graph, nullptr, 0, &kp));
+    }
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t nc;
+    BF_CUDA(cudaGraphAddNode(&nc, graph, &n0, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    BF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    BF_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t keep = st_;
+    st_ = cs;
+    launch_pass(h, 1);
+    st_ = keep;
+    cudaGraph_t captured;
+    cudaError_t e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return bfh::cuda_fail(e, "batch graph capture"); }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return bfh::cuda_fail(e, "batch graph instantiate"); }
+    e = cudaGraphLaunch(exec, st_);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfh::cuda_fail(e, "batch graph launch");
+    return BF_OK;
+}
+
+int Engine::step(int passes) {
+    if (dev_.n == 0) return BF_OK;
+    for (int p = 0; p < passes; ++p) launch_pass(0, 0);
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
+int Engine::read_counters(std::vector<Counters>& out) {
+    out.resize(insts_.size());
+    for (size_t i = 0; i < insts_.size(); ++i)
+        BF_CUDA(cudaMemcpyAsync(&out[i], insts_[i]->view.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st_));
+    BF_CUDA(cudaStreamSynchronize(st_));
+    return BF_OK;
+}
+
+int Engine::finish_instance(InstState* s, int64_t* iters, int32_t* status, int* err) {
+    const long long C = s->a->g.C;
+    k_b_output<<<blocks_for(C), 256, 0, st_>>>(C, s->view.Vkey, s->Vdev);
+    BF_CUDA(cudaGetLastError());
+    if (s->V_host) BF_CUDA(cudaMemcpyAsync(s->V_host, s->Vdev, 8 * (size_t)C, cudaMemcpyDeviceToHost, st_));
+    if (s->mu_host) BF_CUDA(cudaMemcpyAsync(s->mu_host, s->view.mu, (size_t)C, cudaMemcpyDeviceToHost, st_));
+    else BF_CUDA(cudaMemcpyAsync(s->mu_dev_out, s->view.mu, (size_t)C, cudaMemcpyDeviceToDevice, st_));
+    Counters hc;
+    BF_CUDA(cudaMemcpyAsync(&hc, s->view.ctr, sizeof hc, cudaMemcpyDeviceToHost, st_));
+    BF_CUDA(cudaStreamSynchronize(st_));
+    *iters = hc.round;
+    *status = hc.status;
+    *err = hc.err;
+    return BF_OK;
+}
+
+}  // namespace bfb
+
+extern "C" int bf_solve_batch(int32_t n, const bf_abstraction* const* abs, const double* const* G,
+                              const uint8_t* const* target, const uint8_t* const* avoid,
+                              const double* const* terminal, int64_t max_iters, double* const* V,
+                              uint8_t* const* mu, int64_t* iters, int32_t* status, void* stream) {
+    if (n < 0 || (n > 0 && (!abs || !G || !V || !mu || !iters || !status))) {
+        bfh::set_error("bf_solve_batch: NULL argument array");
+        return BF_ERR_INVALID;
+    }
+    if (n == 0) return BF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    bfb::Engine eng(st);
+    std::vector<bfb::InstState*> order(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = eng.add(abs[i], G[i], target ? target[i] : nullptr, avoid ? avoid[i] : nullptr,
+                         terminal ? terminal[i] : nullptr, max_iters, V[i], mu[i], &order[i]);
+        if (rc) return rc;
+    }
+    int rc = eng.rebuild();
+    if (rc) return rc;
+    rc = eng.run_to_completion();
+    if (rc) return rc;
+    int first_err = -1;
+    for (int i = 0; i < n; ++i) {
+        int err = 0;
+        rc = eng.finish_instance(order[i], &iters[i], &status[i], &err);
+        if (rc) return rc;
+        if (err && first_err < 0) first_err = i;
+    }
+    if (first_err >= 0) {
+        bfh::set_error("bf_solve_batch: instance %d has NaN, -inf or |value| > 2^64 in G or the terminal cost",
+                       first_err);
+        return BF_ERR_INVALID;
+    }
+    return BF_OK;
+}

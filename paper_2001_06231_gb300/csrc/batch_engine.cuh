@@ -1,0 +1,93 @@
+// batch_engine.cuh -- the batched form of Algorithm 1: many independent
+// instances (each with its own abstraction, costs, target and avoid set;
+// uneven sizes) advanced together.  A pass is one relax launch per group of
+// instances sharing dimension and storage mode, one planning launch, one
+// propagate launch per group and one finishing launch; each launch covers
+// every unfinished instance, its warps pulling (instance, segment) or
+// (instance, changed cell) work items through per-instance prefix offsets.
+// Instances keep their own pass counters, frontiers and termination, so each
+// result is identical to a solo bf_solve.
+//
+// bf_solve_batch runs the pass loop inside a CUDA graph WHILE node; the
+// server (serve.cu) runs a bounded number of passes per engine step and lets
+// instances join and leave between steps.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "solve_core.cuh"
+
+namespace bfb {
+
+using bfk::Counters;
+using bfk::InstView;
+
+constexpr int kMaxGroups = 8;   // D in 1..4 x {stored, recompute}
+
+// Device-side description of one batch (rebuilt when the instance set changes).
+struct BatchDev {
+    InstView* views;    // [n], ordered by group
+    int* scan;          // [n + 1] exclusive prefix of the per-instance work counts
+    int* totals;        // [kMaxGroups] work items per group
+    int* active;        // [1] unfinished instances
+    int n;
+    int ngroups;
+    int gbeg[kMaxGroups + 1];   // instances of group g are [gbeg[g], gbeg[g + 1])
+};
+
+// Per-instance device state, carved from one buffer.
+struct InstState {
+    const bf_abstraction* a = nullptr;
+    InstView view;
+    void* mem = nullptr;          // owned allocation (state + staging)
+    double* G = nullptr;          // device copies or caller device pointers
+    const unsigned char* target = nullptr;
+    const unsigned char* avoid = nullptr;
+    const double* terminal = nullptr;
+    double* Vdev = nullptr;       // device V output (caller's or staging)
+    double* V_host = nullptr;     // caller host V (copied back at the end) or NULL
+    unsigned char* mu_host = nullptr;
+    unsigned char* mu_dev_out = nullptr;
+    long long cap = 0;
+    int group = 0;
+    bool done = false;
+};
+
+// Engine: owns the device batch description and launches passes.
+class Engine {
+public:
+    explicit Engine(cudaStream_t st) : st_(st) {}
+    ~Engine();
+    // Set up an instance (allocate state, stage inputs, run lines 1-10 of
+    // Algorithm 1).  Inputs may be host or device.  Returns BF_OK or an error.
+    int add(const bf_abstraction* a, const double* G, const unsigned char* target,
+            const unsigned char* avoid, const double* terminal, long long max_iters,
+            double* V, unsigned char* mu, InstState** out);
+    // Rebuild the device description for the current instance list (group order).
+    int rebuild();
+    // Run passes until every instance is done (graph with a WHILE node).
+    int run_to_completion();
+    // Run at most `passes` passes (host loop); returns BF_OK.
+    int step(int passes);
+    // Copy the results of finished instances out; fills *iters/*status.
+    int finish_instance(InstState* s, int64_t* iters, int32_t* status, int* err);
+    // Remove an instance (frees its state).
+    void remove(InstState* s);
+    // Read all counters (host copies, index = position in list()).
+    int read_counters(std::vector<Counters>& out);
+    std::vector<InstState*>& list() { return insts_; }
+    size_t state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, bool stage_V) const;
+
+private:
+    void launch_pass(cudaGraphConditionalHandle h, int use_graph);
+    cudaStream_t st_;
+    std::vector<InstState*> insts_;
+    BatchDev dev_{};
+    void* dev_mem_ = nullptr;
+    size_t dev_mem_bytes_ = 0;
+    int relax_blocks_ = 0, prop_blocks_ = 0;
+    int group_D_[kMaxGroups] = {}, group_rc_[kMaxGroups] = {};
+};
+
+}  // namespace bfb

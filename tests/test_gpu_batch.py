@@ -1,0 +1,68 @@
+"""Batched solve: every instance identical to its solo solve (and to the oracle).
+
+Instances of different dimension, size, storage mode and cost structure are
+solved in one bf_solve_batch call; V, mu, the pass count and the status of
+each must equal a separate bf_solve on the same inputs, which the parity tests
+tie to the CPU oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2001_06231_gb300 as bf
+from paper_2001_06231_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batch_equals_solo_mixed_instances():
+    ws = [wl.unicycle3d(n=(40, 36, 16), n_obstacles=5, seed=1),
+          wl.unicycle3d(n=(70, 64, 24), n_obstacles=12, seed=2, cost_c=0.7),
+          wl.di2d(tau=0.3),
+          wl.di2d(),
+          wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0)))]
+    modes = [bf.MODE_STORED, bf.MODE_RECOMPUTE, bf.MODE_STORED, bf.MODE_RECOMPUTE, bf.MODE_STORED]
+    As = [bf.abs_build_workload(w, mode=m) for w, m in zip(ws, modes)]
+    solo = [bf.bf_solve(A, w.G, target=w.target, avoid=w.avoid) for A, w in zip(As, ws)]
+    res = bf.bf_solve_batch(As, [w.G for w in ws], targets=[w.target for w in ws],
+                            avoids=[w.avoid for w in ws])
+    for r, s in zip(res, solo):
+        assert r["iters"] == s["iters"] and r["status"] == s["status"]
+        assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"])
+    # one instance also against the oracle directly
+    w, A = ws[1], As[1]
+    ref = oracle.solve(w.grid.n, w.grid.periodic, A.export_boxes(), w.G, w.terminal(), w.avoid)
+    assert np.array_equal(res[1]["V"], ref["V"]) and res[1]["iters"] == ref["iters"]
+
+
+def test_batch_same_abstraction_many_costs_and_caps():
+    w = wl.unicycle3d(n=(50, 44, 16), n_obstacles=6)
+    A = bf.abs_build_workload(w)
+    rng = np.random.default_rng(3)
+    Gs, tgs, terms = [], [], []
+    for i in range(6):
+        G = w.G * rng.uniform(0.5, 2.0) + (i % 3) * 0.01
+        Gs.append(G)
+        tgs.append(w.target)
+    # terminal-cost instances mixed in, with a cap
+    T = np.where(w.target.astype(bool), 0.0, math.inf)
+    T[:100] = 1.5
+    res = bf.bf_solve_batch([A] * 7, Gs + [w.G], targets=tgs + [None], avoids=[w.avoid] * 7,
+                            terminals=[None] * 6 + [T], max_iters=40)
+    for i in range(6):
+        s = bf.bf_solve(A, Gs[i], target=tgs[i], avoid=w.avoid, max_iters=40)
+        assert res[i]["iters"] == s["iters"] and res[i]["status"] == s["status"]
+        assert np.array_equal(res[i]["V"], s["V"]) and np.array_equal(res[i]["mu"], s["mu"])
+    s = bf.bf_solve(A, w.G, terminal=T, avoid=w.avoid, max_iters=40)
+    assert np.array_equal(res[6]["V"], s["V"]) and res[6]["iters"] == s["iters"]
+
+
+def test_batch_rejects_nan_instance():
+    w = wl.di2d(tau=0.3)
+    A = bf.abs_build_workload(w)
+    G = w.G.copy()
+    G[5, 2] = np.nan
+    with pytest.raises(bf.BfError):
+        bf.bf_solve_batch([A, A], [w.G, G], targets=[w.target, w.target], avoids=[w.avoid, w.avoid])
