@@ -397,13 +397,151 @@ def batched(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# served form: Poisson arrivals over three resident systems
+# --------------------------------------------------------------------------
+def served(args):
+    import math
+    import queue
+    import threading
+    import torch
+    import paper_2001_06231_gb300 as bf
+    from paper_2001_06231_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(wl.SEED_BASE + 5)
+    fire_target = ((50.0, 250.0), (50.0, 150.0), (-math.radians(30), math.radians(30)), (10.0, 15.0))
+    bases = [wl.di2d(), wl.unicycle3d(n=(100, 100, 32)), wl.fire4d(n=(60, 60, 24, 6), tau=2.0, target=fire_target)]
+    # distinct payloads (fresh seeded targets / fire maps), cycled over the arrivals
+    payloads = []
+    for j in range(args.payloads):
+        k = j % 3
+        seed = int(rng.integers(0, 2**31 - 1))
+        if k == 0:
+            r2 = np.random.default_rng(seed)
+            cx, cy = r2.uniform(-3.5, 3.5, size=2)
+            w = wl.di2d()
+            w.target = wl.box_contains_cells(w.grid, [(cx - .6, cx + .6), (cy - .6, cy + .6)]).astype(np.uint8)
+            w.target &= 1 - w.avoid
+        elif k == 1:
+            r2 = np.random.default_rng(seed)
+            tx, ty = r2.uniform(1.0, 8.0, size=2)
+            w = wl.unicycle3d(n=(100, 100, 32), seed=seed,
+                              target_xy=((tx, tx + 1.0), (ty, ty + 1.0)))
+        else:
+            w = wl.fire4d(n=(60, 60, 24, 6), tau=2.0, seed=seed, target=fire_target)
+        # pinned host payloads (DMA to the device) for both arms
+        pin = (torch.from_numpy(w.G).pin_memory(), torch.from_numpy(w.target).pin_memory(),
+               torch.from_numpy(w.avoid).pin_memory())
+        payloads.append((k, w, pin))
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=args.requests))
+    systems = [(b.kind, b.params, b.substeps, b.grid, b.inputs, b.tau) for b in bases]
+    resident = [bf.abs_build_workload(b) for b in bases]       # for the one-at-a-time arm
+
+    def run_served(times):
+        srv = bf.Server(hbm_budget=int(args.budget_gb * (1 << 30)), max_active=args.max_active,
+                        passes_per_step=args.passes)
+        # warm: one request per system (builds the resident abstractions)
+        for k in range(3):
+            w = payloads[k][1]
+            srv.poll(srv.submit(w.G, target=w.target, avoid=w.avoid, system=systems[k]), wait=True)
+        outs = [(torch.empty(payloads[i][1].ncells, dtype=torch.float64).pin_memory(),
+                 torch.empty(payloads[i][1].ncells, dtype=torch.uint8).pin_memory())
+                for i in range(len(payloads))]
+        ids = [None] * len(times)
+        t0 = time.perf_counter()
+
+        def client():
+            for i, t in enumerate(times):
+                d = t0 + t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                k, w, (G, tg, av) = payloads[i % len(payloads)]
+                Vo, muo = outs[i % len(payloads)]
+                ids[i] = srv.submit(G, target=tg, avoid=av, system=systems[k], borrow=True, V=Vo, mu=muo)
+        th = threading.Thread(target=client)
+        th.start()
+        th.join()
+        res = [srv.poll(rid, wait=True) for rid in ids]
+        srv.close()
+        lat = np.array([r["finish_s"] - r["submit_s"] for r in res])
+        span = max(r["finish_s"] for r in res) - min(r["submit_s"] for r in res)
+        modes = sorted(set(r["mode"] for r in res))
+        return len(times) / span, lat, res, modes
+
+    def run_plain(times):
+        q = queue.Queue()
+        outs = [(torch.empty(payloads[i][1].ncells, dtype=torch.float64).pin_memory(),
+                 torch.empty(payloads[i][1].ncells, dtype=torch.uint8).pin_memory())
+                for i in range(len(payloads))]
+        done = [None] * len(times)
+        t0 = time.perf_counter()
+
+        def worker():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                i, t_sub = item
+                k, w, (G, tg, av) = payloads[i % len(payloads)]
+                Vo, muo = outs[i % len(payloads)]
+                bf.bf_solve(resident[k], G, target=tg, avoid=av, V=Vo, mu=muo)
+                done[i] = (t_sub, time.perf_counter())
+        wt = threading.Thread(target=worker)
+        wt.start()
+        for i, t in enumerate(times):
+            d = t0 + t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            q.put((i, time.perf_counter()))
+        q.put(None)
+        wt.join()
+        lat = np.array([b - a for a, b in done])
+        span = max(b for a, b in done) - min(a for a, b in done)
+        return len(times) / span, lat
+
+    # correctness spot check: a few served results equal solo solves
+    qps_s, lat_s, res_s, modes = run_served(arrivals)
+    for i in range(min(6, len(res_s))):
+        k, w, _ = payloads[i % len(payloads)]
+        ref = bf.bf_solve(resident[k], w.G, target=w.target, avoid=w.avoid)
+        assert ref["iters"] == res_s[i]["iters"] and ref["status"] == res_s[i]["status"]
+    qps_p, lat_p = run_plain(arrivals)
+    sat = np.zeros(args.requests)
+    qps_s_sat, lat_s_sat, _, _ = run_served(sat)
+    qps_p_sat, lat_p_sat = run_plain(sat)
+    pct = lambda a, q: float(np.percentile(a, q)) * 1e3
+    line = {"metric": "queries/s", "value": qps_s, "unit": "queries/s", "n_gpus": 1, "steps": args.requests,
+            "warmup": 3, "ms_per_step": 1e3 / qps_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "served: Poisson %.0f req/s, %d requests cycling %d payloads over di2d 64x64, "
+                                   "unicycle3d 100x100x32, fire4d 60x60x24x6 (tau 2 s); server-resident "
+                                   "abstractions, budget %.0f GB, %d slots, %d passes per engine step" % (
+                                       args.rate, args.requests, args.payloads, args.budget_gb, args.max_active,
+                                       args.passes),
+                       "abstraction_modes": modes},
+            "served": {"qps": qps_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
+                       "saturated_qps": qps_s_sat, "saturated_p50_ms": pct(lat_s_sat, 50),
+                       "saturated_p99_ms": pct(lat_s_sat, 99)},
+            "plain_one_at_a_time": {"qps": qps_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                                    "saturated_qps": qps_p_sat, "saturated_p50_ms": pct(lat_p_sat, 50),
+                                    "saturated_p99_ms": pct(lat_p_sat, 99)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="unicycle3d", choices=["unicycle3d", "fire4d", "di2d", "batched"])
+    ap.add_argument("--workload", default="unicycle3d",
+                    choices=["unicycle3d", "fire4d", "di2d", "batched", "served"])
+    ap.add_argument("--requests", type=int, default=600, help="served: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (1/s)")
+    ap.add_argument("--payloads", type=int, default=36, help="served: distinct request payloads")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="served: device-memory budget")
+    ap.add_argument("--max-active", type=int, default=64, help="served: requests on the device at once")
+    ap.add_argument("--passes", type=int, default=8, help="served: passes per engine step")
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -418,6 +556,8 @@ def main():
         reference_arm(args, rank, world)
     elif args.workload == "batched":
         batched(args)
+    elif args.workload == "served":
+        served(args)
     else:
         ours(args, rank, world, local_rank)
 

@@ -222,39 +222,67 @@ BF_API int bf_solve_batch(int32_t n, const bf_abstraction *const *abs, const dou
                    double *const *V, uint8_t *const *mu, int64_t *iters, int32_t *status,
                    void *stream);
 
-/* Server: continuous batching of solve requests on resident abstractions.
- * Requests are admitted while the device-memory budget and the slot count
- * allow; the engine advances all admitted instances together, retires
- * finished ones and admits waiting ones between device steps. */
+/* Server: continuous batching of solve requests (the served form of the
+ * solver).  A server owns one engine thread and one stream.  Requests are
+ * admitted in arrival order while the device-memory budget and the slot count
+ * allow; the engine advances every admitted request together (a bounded
+ * number of passes per engine step, as in bf_solve_batch), and between steps
+ * retires finished requests (results copied to the request's host buffers)
+ * and admits waiting ones, so requests that arrive while others are on the
+ * GPU join them.  Each result is identical to a solo bf_solve.
+ *
+ * A request names either a resident abstraction (abs, kept alive by the
+ * caller) or a system (dyn, grid, inputs, tau); the server keeps the
+ * abstractions it builds resident and reuses them for later requests with
+ * the same system (compared field by field).  A new abstraction is built in
+ * STORED mode when its boxes fit the remaining budget, else in RECOMPUTE mode
+ * (the memory control of Sec. IV-B). */
 typedef struct bf_server bf_server;
 
 typedef struct {
-    const bf_abstraction *abs;   /* resident abstraction (kept alive by caller) */
-    const double *G;             /* host [C][U], copied at submit               */
-    const uint8_t *target;       /* host [C] or NULL when terminal is given     */
-    const uint8_t *avoid;        /* host [C] or NULL                            */
-    const double *terminal;      /* host [C] or NULL                            */
+    const bf_abstraction *abs;   /* resident abstraction, or NULL: use dyn/grid/inputs/tau */
+    const bf_dynamics *dyn;      /* system of the request when abs == NULL (copied)      */
+    const bf_grid *grid;
+    const bf_inputs *inputs;
+    double tau;
+    const double *G;             /* host [C][U], copied at submit                         */
+    const uint8_t *target;       /* host [C] or NULL when terminal is given               */
+    const uint8_t *avoid;        /* host [C] or NULL                                      */
+    const double *terminal;      /* host [C] or NULL                                      */
     int64_t max_iters;
-    double *V;                   /* host [C] destination, written on completion */
-    uint8_t *mu;                 /* host [C] destination                        */
+    double *V;                   /* host [C] destination, written before done = 1        */
+    uint8_t *mu;                 /* host [C] destination                                  */
+    int32_t flags;               /* BF_REQ_*                                              */
 } bf_request;
 
+/* The caller keeps G, target, avoid and terminal unchanged and alive until the
+ * request is done, so bf_serve_submit does not copy them (pinned host buffers
+ * then go to the device by DMA without an extra host copy). */
+#define BF_REQ_BORROW_INPUTS 1
+
 typedef struct {
-    int32_t done;                /* 1 when V/mu/iters/status are final           */
-    int32_t status;
+    int32_t done;                /* 1 when V/mu/iters/status are final                    */
+    int32_t status;              /* BF_CONVERGED / BF_NEG_CYCLE / BF_ITER_CAP             */
     int64_t iters;
-    int32_t error;               /* BF_OK or the error of this request           */
-    double submit_s, admit_s, finish_s;   /* wall clock (seconds, monotonic)    */
+    int32_t error;               /* BF_OK or the error of this request                    */
+    int32_t mode;                /* storage mode of the abstraction used                  */
+    double submit_s, admit_s, finish_s;   /* steady-clock seconds                         */
 } bf_result;
 
-/* bf_serve_open -- start a server with a device-memory budget in bytes for
- * per-request state and at most max_active concurrently admitted requests. */
-BF_API int bf_serve_open(size_t hbm_budget, int32_t max_active, void *stream, bf_server **out);
-/* bf_serve_submit -- enqueue a request (inputs copied); returns its id. */
+/* bf_serve_open -- start a server.  hbm_budget: device bytes the server may
+ * use for the abstractions it builds plus per-request state; max_active: most
+ * requests on the device at once; passes_per_step: passes per engine step (0
+ * -> 8).  Errors: BF_ERR_INVALID, BF_ERR_CUDA. */
+BF_API int bf_serve_open(size_t hbm_budget, int32_t max_active, int32_t passes_per_step,
+                         bf_server **out);
+/* bf_serve_submit -- enqueue a request (host inputs copied); *id identifies
+ * it.  A request that can never fit the budget completes with BF_ERR_OOM. */
 BF_API int bf_serve_submit(bf_server *srv, const bf_request *req, uint64_t *id);
-/* bf_serve_poll -- state of request id; wait != 0 blocks until done. */
+/* bf_serve_poll -- state of request id; wait != 0 blocks until it is done.
+ * A done request is forgotten after it was polled done once. */
 BF_API int bf_serve_poll(bf_server *srv, uint64_t id, int32_t wait, bf_result *out);
-/* bf_serve_close -- finish all requests and free the server. */
+/* bf_serve_close -- finish every submitted request, stop the engine thread,
+ * free the server and the abstractions it built. */
 BF_API void bf_serve_close(bf_server *srv);
 
 /* bf_last_error -- message of the last failed call on this thread. */

@@ -31,7 +31,8 @@ SCHED_AUTO, SCHED_SEGMENT, SCHED_LIST = 0, 1, 2
 FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 
 EXPORTED = ["abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
-            "abs_free", "bf_solve", "bf_solve_batch", "bf_last_error"]
+            "abs_free", "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
+            "bf_serve_close", "bf_solve_noalloc", "bf_last_error"]
 
 
 class BfError(RuntimeError):
@@ -70,15 +71,20 @@ class SolveOpts(ctypes.Structure):
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("abs", ctypes.c_void_p), ("G", ctypes.c_void_p), ("target", ctypes.c_void_p),
-                ("avoid", ctypes.c_void_p), ("terminal", ctypes.c_void_p), ("max_iters", ctypes.c_int64),
-                ("V", ctypes.c_void_p), ("mu", ctypes.c_void_p)]
+    _fields_ = [("abs", ctypes.c_void_p), ("dyn", ctypes.c_void_p), ("grid", ctypes.c_void_p),
+                ("inputs", ctypes.c_void_p), ("tau", ctypes.c_double), ("G", ctypes.c_void_p),
+                ("target", ctypes.c_void_p), ("avoid", ctypes.c_void_p), ("terminal", ctypes.c_void_p),
+                ("max_iters", ctypes.c_int64), ("V", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("flags", ctypes.c_int32)]
+
+
+REQ_BORROW_INPUTS = 1
 
 
 class Result(ctypes.Structure):
     _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("iters", ctypes.c_int64),
-                ("error", ctypes.c_int32), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
-                ("finish_s", ctypes.c_double)]
+                ("error", ctypes.c_int32), ("mode", ctypes.c_int32), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
 
 
 _lib = None
@@ -105,9 +111,16 @@ def lib():
         L.abs_free.restype = None
         L.bf_solve.argtypes = [P, P, P, P, P, P, P, P, P, P]
         L.bf_solve_batch.argtypes = [i32, P, P, P, P, P, i64, P, P, P, P, P]
+        L.bf_serve_open.argtypes = [ctypes.c_size_t, i32, i32, P]
+        L.bf_serve_submit.argtypes = [P, P, P]
+        L.bf_serve_poll.argtypes = [P, ctypes.c_uint64, i32, P]
+        L.bf_serve_close.argtypes = [P]
+        L.bf_serve_close.restype = None
+        L.bf_solve_noalloc.argtypes = [P, P, P, P, P, i64, P, P, P, P, P]
         L.bf_last_error.restype = ctypes.c_char_p
         for name in ("abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
-                     "bf_solve", "bf_solve_batch"):
+                     "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
+                     "bf_solve_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -296,3 +309,78 @@ def bf_solve_batch(abstractions, Gs, targets=None, avoids=None, terminals=None, 
     _check(lib().bf_solve_batch(n, absa, ga, ta, va, tm if terminals is not None else None, int(max_iters),
                                 Va, ma, it, st, _stream(stream)))
     return [{"V": Vs[i], "mu": mus[i], "iters": it[i], "status": st[i]} for i in range(n)]
+
+
+class Server:
+    """Continuous-batching solve server (bf_serve_*).
+
+    submit() copies the request's host inputs; the result arrays V / mu given
+    (or allocated here) are filled when the request completes.
+    """
+
+    def __init__(self, hbm_budget, max_active=64, passes_per_step=8):
+        h = ctypes.c_void_p()
+        _check(lib().bf_serve_open(int(hbm_budget), int(max_active), int(passes_per_step), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, G, target=None, avoid=None, terminal=None, abstraction=None, system=None,
+               max_iters=0, V=None, mu=None, borrow=False):
+        """system: (kind, params, substeps, grid, inputs, tau) when abstraction is None.
+
+        borrow=True: the arrays are not copied at submit and must stay alive
+        and unchanged until the request is done (they are kept referenced).
+        """
+        keep = []
+        q = Request()
+        if abstraction is not None:
+            q.abs = abstraction.handle.value
+            C = abstraction.ncells
+        else:
+            kind, params, substeps, grid, inputs, tau = system
+            g = make_grid(grid)
+            u = np.ascontiguousarray(np.atleast_2d(inputs), dtype=np.float64)
+            inp = Inputs(u.shape[0], u.shape[1], u.ctypes.data)
+            dyn = Dynamics()
+            dyn.kind = int(kind)
+            dyn.rk4_substeps = int(substeps)
+            for i, p in enumerate(params):
+                dyn.param[i] = float(p)
+            keep += [g, u, inp, dyn]
+            q.dyn, q.grid, q.inputs = ctypes.addressof(dyn), ctypes.addressof(g), ctypes.addressof(inp)
+            q.tau = float(tau)
+            C = int(np.prod([g.n[d] for d in range(g.ndim)]))
+        Gc = _host(G, np.float64)
+        tg = _host(target, np.uint8)
+        av = _host(avoid, np.uint8)
+        tm = _host(terminal, np.float64)
+        V = np.empty(C, dtype=np.float64) if V is None else V
+        mu = np.empty(C, dtype=np.uint8) if mu is None else mu
+        q.G, q.target, q.avoid, q.terminal = _ptr(Gc), _ptr(tg), _ptr(av), _ptr(tm)
+        q.max_iters = int(max_iters)
+        q.V, q.mu = _ptr(V), _ptr(mu)
+        q.flags = REQ_BORROW_INPUTS if borrow else 0
+        rid = ctypes.c_uint64()
+        _check(lib().bf_serve_submit(self.handle, ctypes.byref(q), ctypes.byref(rid)))
+        self._keep[rid.value] = (V, mu, (Gc, tg, av, tm) if borrow else None)
+        return rid.value
+
+    def poll(self, rid, wait=True):
+        """Returns dict(done, status, iters, error, mode, submit_s, admit_s, finish_s[, V, mu])."""
+        r = Result()
+        _check(lib().bf_serve_poll(self.handle, ctypes.c_uint64(rid), 1 if wait else 0, ctypes.byref(r)))
+        out = {k: getattr(r, k) for k, _ in Result._fields_}
+        if r.done:
+            out["V"], out["mu"], _ = self._keep.pop(rid)
+        return out
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().bf_serve_close(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

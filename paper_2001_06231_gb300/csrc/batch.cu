@@ -111,12 +111,25 @@ __device__ __forceinline__ int find_instance(const int* __restrict__ scan, int b
     return lo;
 }
 
+// After an instance's set-up (lines 1-10 of Algorithm 1): F1 is in list 0;
+// decide whether it loops at all.  Afterwards the instance looks like one
+// whose previous pass just closed, so it can join a running batch.
+__global__ void k_b_start(Counters* k) {
+    k->nchg = 0;
+    const bool cont = k->err == 0 && k->nseg[0] > 0 && k->cap > 0;
+    if (!cont) {
+        k->done = 1;
+        k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
+    }
+}
+
 // Planning (one block of 1024 threads).
-//   mode 0 (after set-up): decide which instances start looping; work = segments.
-//   mode 1 (after relax):  work = changed cells.
-//   mode 2 (after propagate): close the pass of each unfinished instance; work = segments.
-// Writes scan[0..n], totals per group and, in modes 0 and 2, the number of
-// unfinished instances (and the WHILE condition of the graph).
+//   mode 1 (after relax):  work = changed cells of the pass.
+//   mode 2 (after propagate): close the pass of each unfinished instance;
+//                             work = segments of the next pass.
+//   mode 3 (instance set changed): work = segments of the next pass.
+// Writes scan[0..n] and, in modes 2 and 3, the number of unfinished
+// instances (and the WHILE condition of the graph).
 __global__ void __launch_bounds__(1024) k_b_plan(BatchDev b, int mode, cudaGraphConditionalHandle h,
                                                  int use_graph) {
     __shared__ int sums[1024];
@@ -133,19 +146,12 @@ __global__ void __launch_bounds__(1024) k_b_plan(BatchDev b, int mode, cudaGraph
         Counters* k = v.ctr;
         int cnt = 0;
         if (!k->done) {
-            if (mode == 0) {
-                k->nchg = 0;
-                const bool cont = k->err == 0 && k->nseg[0] > 0 && k->cap > 0;
-                if (!cont) {
-                    k->done = 1;
-                    k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
-                } else {
-                    cnt = k->nseg[0];
-                }
-            } else if (mode == 1) {
+            if (mode == 1) {
                 cnt = k->nchg;
-            } else {
+            } else if (mode == 2) {
                 if (finish_pass(v)) cnt = k->nseg[k->round & 1];
+            } else {
+                cnt = k->nseg[k->round & 1];
             }
             if (!k->done) ++alive;
         }
@@ -245,6 +251,16 @@ Engine::~Engine() {
     insts_.clear();
     if (dev_mem_) cudaFreeAsync(dev_mem_, st_);
     cudaStreamSynchronize(st_);
+}
+
+size_t Engine::state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, bool stage_V) const {
+    const size_t C = (size_t)a->g.C, U = (size_t)a->g.U, S = (C + 31) / 32;
+    size_t o = r256(sizeof(Counters)) + 2 * r256(8 * C) + r256(C) + 3 * r256(4 * S) + r256(4 * C) +
+               r256(8 * C * U);
+    if (stage_G) o += r256(8 * C * U);
+    if (stage_T) o += r256(8 * C) + r256(C) + r256(C);   // terminal or target, plus avoid
+    if (stage_V) o += r256(8 * C);
+    return o;
 }
 
 static int group_of(const bf_abstraction* a) {
@@ -352,6 +368,7 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
         case 3: k_b_propagate_init<3><<<pb, 256, 0, st_>>>(v); break;
         default: k_b_propagate_init<4><<<pb, 256, 0, st_>>>(v); break;
     }
+    k_b_start<<<1, 1, 0, st_>>>(v.ctr);
     BF_CUDA(cudaGetLastError());
     insts_.push_back(s);
     if (out) *out = s;
@@ -400,9 +417,14 @@ int Engine::rebuild() {
     dev_.totals = reinterpret_cast<int*>(m);
     m += r256(4 * kMaxGroups);
     dev_.active = reinterpret_cast<int*>(m);
-    std::vector<InstView> hv(n);
-    for (int i = 0; i < n; ++i) hv[i] = insts_[i]->view;
-    if (n) BF_CUDA(cudaMemcpyAsync(dev_.views, hv.data(), sizeof(InstView) * n, cudaMemcpyHostToDevice, st_));
+    host_views_.resize(n);
+    for (int i = 0; i < n; ++i) host_views_[i] = insts_[i]->view;
+    if (n)
+        BF_CUDA(cudaMemcpyAsync(dev_.views, host_views_.data(), sizeof(InstView) * n, cudaMemcpyHostToDevice,
+                                st_));
+    // work offsets of the next pass for the new instance set
+    if (n) k_b_plan<<<1, 1024, 0, st_>>>(dev_, 3, 0, 0);
+    BF_CUDA(cudaGetLastError());
     if (!relax_blocks_) {
         relax_blocks_ = n_sms() * 4;
         prop_blocks_ = n_sms() * 4;
@@ -444,8 +466,6 @@ void Engine::launch_pass(cudaGraphConditionalHandle h, int use_graph) {
 
 int Engine::run_to_completion() {
     if (dev_.n == 0) return BF_OK;
-    k_b_plan<<<1, 1024, 0, st_>>>(dev_, 0, 0, 0);
-    BF_CUDA(cudaGetLastError());
     cudaGraph_t graph;
     BF_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle h;

@@ -77,12 +77,15 @@ public:
     // Read all counters (host copies, index = position in list()).
     int read_counters(std::vector<Counters>& out);
     std::vector<InstState*>& list() { return insts_; }
+    // Device bytes add() allocates for an instance (upper bound when staging).
     size_t state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, bool stage_V) const;
+    cudaStream_t stream() const { return st_; }
 
 private:
     void launch_pass(cudaGraphConditionalHandle h, int use_graph);
     cudaStream_t st_;
     std::vector<InstState*> insts_;
+    std::vector<InstView> host_views_;   // kept alive until the async copy is done
     BatchDev dev_{};
     void* dev_mem_ = nullptr;
     size_t dev_mem_bytes_ = 0;

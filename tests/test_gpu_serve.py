@@ -1,0 +1,84 @@
+"""Served form: continuous batching gives every request the result it gets alone.
+
+Requests over three systems (2-D, 3-D, 4-D; caller-owned and server-built
+abstractions) are submitted in waves while earlier ones are still on the GPU;
+each result must equal a solo bf_solve of the same inputs, bit for bit.  A
+small memory budget forces the server to build a recompute-mode abstraction,
+and a request that can never fit completes with BF_ERR_OOM.
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import paper_2001_06231_gb300 as bf
+from paper_2001_06231_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def system_of(w):
+    return (w.kind, w.params, w.substeps, w.grid, w.inputs, w.tau)
+
+
+def test_results_alone_equal_results_in_the_mix():
+    rng = np.random.default_rng(5)
+    base = [wl.di2d(tau=0.3), wl.unicycle3d(n=(60, 56, 24), n_obstacles=8),
+            wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0)))]
+    A_user = bf.abs_build_workload(base[1])                       # a caller-owned abstraction
+    reqs = []
+    for i in range(18):
+        k = i % 3
+        w = base[k]
+        G = w.G * (1.0 + 0.25 * rng.integers(0, 4))
+        tgt = w.target.copy()
+        if k == 0:
+            tgt = np.roll(tgt, int(rng.integers(-300, 300)))
+            tgt &= 1 - w.avoid
+        reqs.append((k, G, tgt))
+    srv = bf.Server(hbm_budget=8 << 30, max_active=5, passes_per_step=4)
+    ids = []
+    for wave in range(3):                                          # later waves join a running engine
+        for k, G, tgt in reqs[wave * 6:(wave + 1) * 6]:
+            w = base[k]
+            if k == 1 and wave % 2 == 0:
+                rid = srv.submit(G, target=tgt, avoid=w.avoid, abstraction=A_user)
+            else:
+                rid = srv.submit(G, target=tgt, avoid=w.avoid, system=system_of(w))
+            ids.append(rid)
+        time.sleep(0.01)
+    results = [srv.poll(rid, wait=True) for rid in ids]
+    srv.close()
+    solo_abs = [bf.abs_build_workload(w) for w in base]
+    overlapped = 0
+    for (k, G, tgt), r in zip(reqs, results):
+        assert r["done"] == 1 and r["error"] == 0
+        s = bf.bf_solve(solo_abs[k], G, target=tgt, avoid=base[k].avoid)
+        assert r["iters"] == s["iters"] and r["status"] == s["status"]
+        assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"])
+    # requests really shared the device: some were admitted before others finished
+    for a in results:
+        for b in results:
+            if a is not b and a["admit_s"] < b["finish_s"] and b["admit_s"] < a["finish_s"]:
+                overlapped += 1
+    assert overlapped > 0
+
+
+def test_small_budget_builds_recompute_mode_and_rejects_oversized():
+    w = wl.unicycle3d(n=(60, 56, 24), n_obstacles=8)
+    C, U, D = w.ncells, w.ninputs, 3
+    stored_boxes = C * U * 4 * D
+    state = 2 * 8 * C + C + 4 * C + 2 * 8 * C * U + 8 * C + 2 * C + 8 * C + 64 * 1024
+    budget = state + C * 2 * D * 2 + C * D * 8 + stored_boxes // 2     # boxes do not fit, the rest does
+    srv = bf.Server(hbm_budget=budget, max_active=2)
+    rid = srv.submit(w.G, target=w.target, avoid=w.avoid, system=system_of(w))
+    r = srv.poll(rid, wait=True)
+    assert r["error"] == 0 and r["mode"] == bf.MODE_RECOMPUTE
+    s = bf.bf_solve(bf.abs_build_workload(w), w.G, target=w.target, avoid=w.avoid)
+    assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"]) and r["iters"] == s["iters"]
+    big = wl.unicycle3d(n=(200, 200, 64), n_obstacles=0)
+    rid = srv.submit(big.G, target=big.target, system=system_of(big))
+    r = srv.poll(rid, wait=True)
+    assert r["done"] == 1 and r["error"] == -2                      # BF_ERR_OOM
+    srv.close()
