@@ -70,6 +70,18 @@ def algorithmic_bytes_per_pair(w):
     return 4 * w.grid.ndim + 8
 
 
+def whole_job(units, seconds, dist=None, device=None):
+    """Whole-job throughput over ranks: (sum of units) / (max of seconds)."""
+    if dist is None:
+        return units / seconds, units, seconds
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(t.item()), float(u.item()), float(t.item())
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
@@ -244,13 +256,8 @@ def ours(args, rank, world, local_rank):
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    step_s = ms_max / 1e3 / args.steps
-    value = canonical * world / step_s
+    value, _, t_max = whole_job(canonical * args.steps, ms / 1e3, dist, dev)
+    step_s = t_max / args.steps
 
     # end to end through the public API with pinned host buffers
     Gh = torch.from_numpy(w.G).pin_memory()
@@ -267,12 +274,7 @@ def ours(args, rank, world, local_rank):
     for _ in range(ksteps):
         bf.bf_solve(A, Gh, target=tgh, avoid=avh, V=Vh, mu=muh, stream=stream)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ksteps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = canonical * world / e2e_s
+    e2e_value, _, _ = whole_job(canonical * ksteps, time.perf_counter() - t0, dist, dev)
     h2d = w.G.nbytes + w.target.nbytes + w.avoid.nbytes
     d2h = 8 * C + C
 

@@ -1,0 +1,75 @@
+"""Host-side checks that need no GPU: the C ABI library and its exports, the
+input generators, and the multi-rank aggregation of bench.py (gloo ranks)."""
+import ctypes
+import os
+import re
+import socket
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "bfgpu.h")).read()
+    return sorted(set(re.findall(r"BF_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)))
+
+
+def test_library_loads_and_exports_every_declared_function():
+    from paper_2001_06231_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    names = header_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding lists the same functions
+    import paper_2001_06231_gb300 as bf
+    assert sorted(bf.EXPORTED) == names
+
+
+def test_workload_generators_are_deterministic():
+    from paper_2001_06231_gb300 import workloads as wl
+    a, b = wl.unicycle3d(n=(40, 30, 16)), wl.unicycle3d(n=(40, 30, 16))
+    assert np.array_equal(a.avoid, b.avoid) and np.array_equal(a.target, b.target)
+    assert np.array_equal(a.G, b.G)
+    c = wl.unicycle3d(n=(40, 30, 16), seed=99)
+    assert not np.array_equal(a.avoid, c.avoid)
+    d = wl.di2d()
+    assert d.target.sum() == 36 and d.ncells == 4096
+    f = wl.fire4d(n=(20, 20, 12, 4), target=((0, 400), (0, 400), (-1.0, 1.0), (10, 15)))
+    assert f.G.min() < 0 < f.G.max()          # negative costs over fire
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    units = 1000.0 * (rank + 1)          # ranks solve different amounts of work
+    seconds = 0.5 + 0.25 * rank          # and take different times
+    v, u, t = bench.whole_job(units, seconds, dist, "cpu")
+    out.put((rank, v, u, t))
+    dist.destroy_process_group()
+
+
+def test_bench_whole_job_aggregation_over_gloo_ranks():
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, v, u, t in res:
+        assert u == 3000.0 and t == 0.75 and abs(v - 4000.0) < 1e-9
