@@ -65,9 +65,9 @@ def make_workload(name, rank=0):
     return w, desc
 
 
-def algorithmic_bytes_per_pair(w):
-    # box record (4 * D bytes) + running cost (8 bytes): SURVEY section 8(d)
-    return 4 * w.grid.ndim + 8
+def algorithmic_bytes_per_pair(A):
+    """HBM bytes one relaxation must stream: its box record + its cost (8 B)."""
+    return A.box_record_bytes + 8
 
 
 def whole_job(units, seconds, dist=None, device=None):
@@ -285,7 +285,7 @@ def ours(args, rank, world, local_rank):
         peaks = json.load(open(pk))
     peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    bpp = algorithmic_bytes_per_pair(w)
+    bpp = algorithmic_bytes_per_pair(A)
     bytes_per_launch = executed * bpp / max(1, passes)
     achieved = bytes_per_launch / (relax_ms_avg / 1e3) / 1e9
     traffic = None
@@ -318,7 +318,7 @@ def ours(args, rank, world, local_rank):
                      "peak_source": peak_src, "relax_ms_per_launch": relax_ms_avg,
                      "propagate_ms_per_launch": prop_ms_avg,
                      "bytes_per_launch": bytes_per_launch,
-                     "bytes_note": "executed (cell,input) pairs per launch x %d B (box %d B + G 8 B)" % (
+                     "bytes_note": "executed (cell,input) pairs per launch x %d B (box record %d B + G 8 B)" % (
                          bpp, bpp - 8)},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -153,9 +153,13 @@ BF_API int abs_export_boxes(const bf_abstraction *abs, int16_t *out, void *strea
  * periodic dim the offsets are taken mod n).  lo[0] > hi[0] = empty. */
 BF_API int abs_export_pred(const bf_abstraction *abs, int16_t *out, void *stream);
 
-/* abs_info -- sizes of an abstraction; any out pointer may be NULL. */
+/* abs_info -- sizes of an abstraction; any out pointer may be NULL.
+ * box_record_bytes: bytes per stored (cell, input) box -- 4 or 8 for the
+ * compact relative records (per dim an 8-bit offset from the cell and an
+ * 8-bit width; used whenever every box fits), 4*D for 16-bit absolute
+ * records, 0 in RECOMPUTE mode. */
 BF_API int abs_info(const bf_abstraction *abs, int64_t *ncells, int32_t *ninputs,
-             int32_t *ndim, int32_t *mode, int64_t *device_bytes);
+             int32_t *ndim, int32_t *mode, int64_t *device_bytes, int32_t *box_record_bytes);
 
 /* abs_free -- release an abstraction (NULL is a no-op).  The caller must not
  * free it while a solve on it is running. */

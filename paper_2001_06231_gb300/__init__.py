@@ -106,7 +106,7 @@ def lib():
         L.abs_from_boxes.argtypes = [P, i32, P, P, P]
         L.abs_export_boxes.argtypes = [P, P, P]
         L.abs_export_pred.argtypes = [P, P, P]
-        L.abs_info.argtypes = [P, P, P, P, P, P]
+        L.abs_info.argtypes = [P, P, P, P, P, P, P]
         L.abs_free.argtypes = [P]
         L.abs_free.restype = None
         L.bf_solve.argtypes = [P, P, P, P, P, P, P, P, P, P]
@@ -181,12 +181,12 @@ class Abstraction:
     def __init__(self, handle, grid):
         self.handle = ctypes.c_void_p(handle)
         self.grid = grid
-        nc, nu, nd, md, nb = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(),
-                              ctypes.c_int64())
+        nc, nu, nd, md, nb, rb = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(),
+                                  ctypes.c_int64(), ctypes.c_int32())
         _check(lib().abs_info(self.handle, ctypes.byref(nc), ctypes.byref(nu), ctypes.byref(nd),
-                              ctypes.byref(md), ctypes.byref(nb)))
+                              ctypes.byref(md), ctypes.byref(nb), ctypes.byref(rb)))
         self.ncells, self.ninputs, self.ndim = nc.value, nu.value, nd.value
-        self.mode, self.device_bytes = md.value, nb.value
+        self.mode, self.device_bytes, self.box_record_bytes = md.value, nb.value, rb.value
 
     def export_boxes(self, out=None, stream=None):
         if out is None:

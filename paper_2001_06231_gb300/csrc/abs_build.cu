@@ -123,16 +123,86 @@ __global__ void k_import_boxes(GridDesc g, const short* __restrict__ ext, void* 
 
 template <int D>
 __global__ void k_export_boxes(GridDesc g, DynDesc dd, const double* __restrict__ inputs,
-                               const void* __restrict__ boxes, short* ext) {
+                               const void* __restrict__ boxes, int fmt, short* ext) {
     const long long total = g.C * g.U;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
          p += (long long)gridDim.x * blockDim.x) {
         const int u = (int)(p / g.C);
         const long long c = p - (long long)u * g.C;
-        Box<D> b = boxes ? load_box<D>(boxes, p) : make_box<D>(dd, g, inputs, c, u);
+        Box<D> b;
+        if (fmt == kBoxWide) {
+            b = load_box<D>(boxes, p);
+        } else if (fmt == kBoxRecompute) {
+            b = make_box<D>(dd, g, inputs, c, u);
+        } else {
+            const unsigned long long r = D <= 2 ? reinterpret_cast<const unsigned*>(boxes)[p]
+                                                : reinterpret_cast<const unsigned long long*>(boxes)[p];
+            if (((r >> 8) & 0x7F) == 0) {
+                b.lo[0] = kBlocked;
+#pragma unroll
+                for (int d = 1; d < D; ++d) b.lo[d] = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) b.hi[d] = 0;
+            } else {
+                int k[4];
+                cell_coords(g, c, k);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const int w = (int)((r >> (16 * d + 8)) & 0x7F);
+                    int lo = k[d] + (int)(signed char)((r >> (16 * d)) & 0xFF);
+                    if (g.periodic[d]) {
+                        if (lo < 0) lo += g.n[d];
+                        else if (lo >= g.n[d]) lo -= g.n[d];
+                    }
+                    b.lo[d] = lo;
+                    b.hi[d] = lo + w - 1;
+                }
+            }
+        }
         short* e = ext + (c * g.U + u) * (2 * D);
 #pragma unroll
         for (int d = 0; d < D; ++d) { e[d] = (short)b.lo[d]; e[D + d] = (short)b.hi[d]; }
+    }
+}
+
+// Wide absolute records -> compact relative records (see solve_core.cuh):
+// per dim the lower corner relative to the cell (int8, periodic dims reduced
+// to [-n/2, n/2)) and the width (1..127); width 0 on dim 0 = blocked; bit 7
+// of dim 0's width byte = the box wraps around a periodic dim for this cell.
+// Sets *fail when some box does not fit the format.
+template <int D>
+__global__ void k_to_compact(GridDesc g, const void* __restrict__ wide, void* compact, int* fail) {
+    const long long total = g.C * g.U;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long c = p - (long long)u * g.C;
+        const Box<D> b = load_box<D>(wide, p);
+        unsigned long long rec = 0;
+        if (b.lo[0] != kBlocked) {
+            int k[4];
+            cell_coords(g, c, k);
+            bool wrap = false, bad = false;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int n = g.n[d];
+                const int w = b.hi[d] - b.lo[d] + 1;
+                int rel = b.lo[d] - k[d];
+                if (g.periodic[d]) {
+                    rel %= n;
+                    if (rel < 0) rel += n;
+                    if (rel >= n - n / 2) rel -= n;
+                    wrap |= (k[d] + rel < 0) || (k[d] + rel + w > n);
+                }
+                bad |= w > 127 || rel < -128 || rel > 127;
+                rec |= (unsigned long long)(unsigned char)(signed char)rel << (16 * d);
+                rec |= (unsigned long long)(w & 0x7F) << (16 * d + 8);
+            }
+            if (wrap) rec |= 0x80ull << 8;
+            if (bad) atomicExch(fail, 1);
+        }
+        if (D <= 2) reinterpret_cast<unsigned*>(compact)[p] = (unsigned)rec;
+        else reinterpret_cast<unsigned long long*>(compact)[p] = rec;
     }
 }
 
@@ -282,6 +352,45 @@ static int build_pred(bf_abstraction* a, cudaStream_t st) {
     }
 }
 
+// Replace the wide records by compact ones when every box fits the format.
+template <int D>
+static int to_compact_t(bf_abstraction* a, cudaStream_t st) {
+    const size_t rec = D <= 2 ? 4 : 8;
+    const size_t bytes = rec * (size_t)a->g.C * a->g.U;
+    void* comp = nullptr;
+    int* d_fail = nullptr;
+    int h_fail = 0;
+    BF_CUDA(cudaMalloc(&comp, bytes));
+    cudaError_t e = cudaMalloc((void**)&d_fail, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_fail, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        k_to_compact<D><<<grid_blocks(a->g.C * a->g.U, 256), 256, 0, st>>>(a->g, a->d_boxes, comp, d_fail);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_fail, d_fail, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_fail);
+    if (e != cudaSuccess) { cudaFree(comp); return bfh::cuda_fail(e, "compact box records"); }
+    if (h_fail) {                          // keep the wide records
+        cudaFree(comp);
+        return BF_OK;
+    }
+    cudaFree(a->d_boxes);
+    a->d_boxes = comp;
+    a->box_fmt = kBoxCompact;
+    a->bytes = a->bytes - box_bytes(a->g) + bytes;
+    return BF_OK;
+}
+
+static int to_compact(bf_abstraction* a, cudaStream_t st) {
+    switch (a->g.D) {
+        case 1: return to_compact_t<1>(a, st);
+        case 2: return to_compact_t<2>(a, st);
+        case 3: return to_compact_t<3>(a, st);
+        default: return to_compact_t<4>(a, st);
+    }
+}
+
 static bf_abstraction* new_abs() {
     bf_abstraction* a = new bf_abstraction;
     memset(a, 0, sizeof *a);
@@ -353,11 +462,13 @@ extern "C" int abs_build(const bf_dynamics* dyn, const bf_grid* grid, const bf_i
             default: k_build_boxes<4><<<nb, 128, 0, st>>>(dd, a->g, a->d_inputs, a->d_boxes); break;
         }
     }
+    a->box_fmt = mode == BF_MODE_STORED ? kBoxWide : kBoxRecompute;
     rc = build_pred(a, st);
     if (rc == BF_OK) {
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = bfh::cuda_fail(e, "abs_build kernels");
     }
+    if (rc == BF_OK && mode == BF_MODE_STORED) rc = to_compact(a, st);
     if (rc) { abs_free(a); return rc; }
     *out = a;
     return BF_OK;
@@ -413,11 +524,13 @@ extern "C" int abs_from_boxes(const bf_grid* grid, int32_t ninputs, const int16_
         bfh::set_error("abs_from_boxes: %llu malformed boxes", h_bad);
         return BF_ERR_INVALID;
     }
+    a->box_fmt = kBoxWide;
     rc = build_pred(a, st);
     if (rc == BF_OK) {
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = bfh::cuda_fail(e, "abs_from_boxes pred");
     }
+    if (rc == BF_OK) rc = to_compact(a, st);
     if (rc) { abs_free(a); return rc; }
     *out = a;
     return BF_OK;
@@ -433,10 +546,10 @@ extern "C" int abs_export_boxes(const bf_abstraction* a, int16_t* out, void* str
     DynDesc dd = make_dyndesc(a);
     const int nb = grid_blocks(a->g.C * a->g.U, 128);
     switch (a->g.D) {
-        case 1: k_export_boxes<1><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
-        case 2: k_export_boxes<2><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
-        case 3: k_export_boxes<3><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
-        default: k_export_boxes<4><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, dst); break;
+        case 1: k_export_boxes<1><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
+        case 2: k_export_boxes<2><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
+        case 3: k_export_boxes<3><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
+        default: k_export_boxes<4><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
     }
     BF_CUDA(cudaGetLastError());
     if (!dev) {
@@ -456,12 +569,15 @@ extern "C" int abs_export_pred(const bf_abstraction* a, int16_t* out, void* stre
 }
 
 extern "C" int abs_info(const bf_abstraction* a, int64_t* ncells, int32_t* ninputs, int32_t* ndim,
-                        int32_t* mode, int64_t* device_bytes) {
+                        int32_t* mode, int64_t* device_bytes, int32_t* box_record_bytes) {
     if (!a) { bfh::set_error("abs_info: NULL abstraction"); return BF_ERR_INVALID; }
     if (ncells) *ncells = a->g.C;
     if (ninputs) *ninputs = a->g.U;
     if (ndim) *ndim = a->g.D;
     if (mode) *mode = a->mode;
     if (device_bytes) *device_bytes = (int64_t)a->bytes;
+    if (box_record_bytes)
+        *box_record_bytes = a->box_fmt == kBoxCompact ? (a->g.D <= 2 ? 4 : 8)
+                          : a->box_fmt == kBoxWide ? 4 * a->g.D : 0;
     return BF_OK;
 }

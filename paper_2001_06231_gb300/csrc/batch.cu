@@ -1,13 +1,14 @@
 // batch.cu -- bf_solve_batch and the batched pass engine (batch_engine.cuh).
 //
-// Work distribution: after each phase a one-block planning kernel turns the
-// per-instance work counts (segments of the current frontier, or changed
-// cells) into an exclusive prefix over the instance list, ordered by group.
-// A relax (or propagate) launch for group g then has scan[gend] - scan[gbeg]
-// work items; warp w takes item k, finds its instance by binary search over
-// the prefix and runs the same per-warp routine as the single solve.  The
-// planning kernel after propagate also closes the pass of every unfinished
-// instance (finish_pass) and counts the instances still running.
+// Work distribution: one-block planning kernels turn the per-instance work
+// counts (32-cell chunks of the current frontier, changed cells, 256-word
+// chunks of the frontier bitmap) into exclusive prefixes over the instance
+// list, ordered by group.  A relax (or propagate) launch for group g then has
+// scan[gend] - scan[gbeg] work items; warp w takes item k, finds its instance
+// by binary search over the prefix and runs the same per-warp routine as the
+// single solve.  The planning kernel after the compaction also closes the
+// pass of every unfinished instance (finish_pass) and counts the instances
+// still running.
 #include <math_constants.h>
 
 #include <algorithm>
@@ -81,13 +82,29 @@ __global__ void k_b_values(long long C, const double* __restrict__ terminal,
     if (bad) atomicOr(&ctr->err, 1);
 }
 
+__global__ void k_b_tables(InstView v) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < v.g.C;
+         c += (long long)gridDim.x * blockDim.x)
+        table_entry(v, c);
+}
+
+// Set-up tail of one instance: pred of the finite cells -> F2 bits.
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_b_propagate_init(InstView v) {
     const int nchg = v.ctr->nchg;
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
-        propagate_cell<D>(v, v.chg[i], 0, false);
+        propagate_cell<D>(v, v.chg[i], false);
+}
+
+// Set-up tail of one instance: compact F1 and decide whether it loops.  The
+// instance then looks like one whose previous pass just closed, so it can
+// join a running batch.
+__global__ void __launch_bounds__(256) k_b_compact_init(InstView v, long long nwords) {
+    for (long long wb = (long long)blockIdx.x * blockDim.x; wb < nwords; wb += (long long)gridDim.x * blockDim.x)
+        compact_words(v, (int)wb, (int)nwords);
+    if (last_block_done(&v.ctr->blocks_done)) start_loop(v);
 }
 
 __global__ void k_b_output(long long C, const long long* __restrict__ Vkey, double* V) {
@@ -111,57 +128,16 @@ __device__ __forceinline__ int find_instance(const int* __restrict__ scan, int b
     return lo;
 }
 
-// After an instance's set-up (lines 1-10 of Algorithm 1): F1 is in list 0;
-// decide whether it loops at all.  Afterwards the instance looks like one
-// whose previous pass just closed, so it can join a running batch.
-__global__ void k_b_start(Counters* k) {
-    k->nchg = 0;
-    const bool cont = k->err == 0 && k->nseg[0] > 0 && k->cap > 0;
-    if (!cont) {
-        k->done = 1;
-        k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
-    }
-}
-
-// Planning (one block of 1024 threads).
-//   mode 1 (after relax):  work = changed cells of the pass.
-//   mode 2 (after propagate): close the pass of each unfinished instance;
-//                             work = segments of the next pass.
-//   mode 3 (instance set changed): work = segments of the next pass.
-// Writes scan[0..n] and, in modes 2 and 3, the number of unfinished
-// instances (and the WHILE condition of the graph).
-__global__ void __launch_bounds__(1024) k_b_plan(BatchDev b, int mode, cudaGraphConditionalHandle h,
-                                                 int use_graph) {
-    __shared__ int sums[1024];
-    __shared__ int active;
+// Exclusive prefix over the n per-instance counts already stored in out[0..n)
+// (one block; each thread owns a contiguous chunk).  out[n] = total.
+__device__ void block_exclusive_scan(int* out, int n, int* sums) {
     const int t = threadIdx.x, bd = blockDim.x;
-    if (t == 0) active = 0;
-    __syncthreads();
-    const int n = b.n;
     const int chunk = (n + bd - 1) / bd;
     const int i0 = min(n, t * chunk), i1 = min(n, i0 + chunk);
-    int local = 0, alive = 0;
-    for (int i = i0; i < i1; ++i) {
-        const InstView& v = b.views[i];
-        Counters* k = v.ctr;
-        int cnt = 0;
-        if (!k->done) {
-            if (mode == 1) {
-                cnt = k->nchg;
-            } else if (mode == 2) {
-                if (finish_pass(v)) cnt = k->nseg[k->round & 1];
-            } else {
-                cnt = k->nseg[k->round & 1];
-            }
-            if (!k->done) ++alive;
-        }
-        b.scan[i] = cnt;
-        local += cnt;
-    }
-    if (alive) atomicAdd(&active, alive);
+    int local = 0;
+    for (int i = i0; i < i1; ++i) local += out[i];
     sums[t] = local;
     __syncthreads();
-    // inclusive scan of the per-thread sums (Hillis-Steele)
     for (int off = 1; off < bd; off <<= 1) {
         const int x = t >= off ? sums[t - off] : 0;
         __syncthreads();
@@ -170,15 +146,57 @@ __global__ void __launch_bounds__(1024) k_b_plan(BatchDev b, int mode, cudaGraph
     }
     int run = t > 0 ? sums[t - 1] : 0;
     for (int i = i0; i < i1; ++i) {
-        const int c = b.scan[i];
-        b.scan[i] = run;
+        const int c = out[i];
+        out[i] = run;
         run += c;
     }
     __syncthreads();
-    if (t == 0) {
-        b.scan[n] = sums[bd - 1];
-        for (int g = 0; g < b.ngroups; ++g) b.totals[g] = 0;   // totals are read from scan
-        if (mode != 1) {
+    if (t == 0) out[n] = sums[bd - 1];
+    __syncthreads();
+}
+
+// Planning (one block of 1024 threads).
+//   mode 1 (after relax):      prefixes of the changed cells and of the
+//                              compaction chunks of every unfinished instance.
+//   mode 2 (after compaction): close the pass of every unfinished instance;
+//                              prefix of the next pass's relax chunks.
+//   mode 3 (instance set changed): prefix of the next pass's relax chunks.
+// In modes 2 and 3 also counts the unfinished instances (and sets the WHILE
+// condition of the graph).
+__global__ void __launch_bounds__(1024) k_b_plan(BatchDev b, int mode, cudaGraphConditionalHandle h,
+                                                 int use_graph) {
+    __shared__ int sums[1024];
+    __shared__ int active;
+    const int t = threadIdx.x, bd = blockDim.x;
+    if (t == 0) active = 0;
+    __syncthreads();
+    const int n = b.n;
+    int alive = 0;
+    for (int i = t; i < n; i += bd) {
+        const InstView& v = b.views[i];
+        Counters* k = v.ctr;
+        if (mode == 1) {
+            const bool run = !k->done;
+            b.scan_chg[i] = run ? k->nchg : 0;
+            b.scan_cmp[i] = run ? (int)((((v.g.C + 31) >> 5) + 255) >> 8) : 0;
+        } else {
+            int cnt = 0;
+            if (!k->done) {
+                if (mode == 2) finish_pass(v);
+                if (!k->done) cnt = (k->ncur + 31) >> 5;
+            }
+            if (!k->done) ++alive;
+            b.scan[i] = cnt;
+        }
+    }
+    if (alive) atomicAdd(&active, alive);
+    __syncthreads();
+    if (mode == 1) {
+        block_exclusive_scan(b.scan_chg, n, sums);
+        block_exclusive_scan(b.scan_cmp, n, sums);
+    } else {
+        block_exclusive_scan(b.scan, n, sums);
+        if (t == 0) {
             *b.active = active;
             if (use_graph) cudaGraphSetConditional(h, active > 0 ? 1 : 0);
         }
@@ -189,8 +207,8 @@ __global__ void k_b_cond(const int* active, cudaGraphConditionalHandle h) {
     cudaGraphSetConditional(h, *active > 0 ? 1 : 0);
 }
 
-template <int D, bool RECOMP>
-__global__ void __launch_bounds__(256, RECOMP ? 2 : 4) k_b_relax(BatchDev b, int g) {
+template <int D, int FMT>
+__global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_b_relax(BatchDev b, int g) {
     const int beg = b.gbeg[g], end = b.gbeg[g + 1];
     if (beg >= end) return;
     const int base = b.scan[beg], total = b.scan[end] - base;
@@ -200,10 +218,9 @@ __global__ void __launch_bounds__(256, RECOMP ? 2 : 4) k_b_relax(BatchDev b, int
         const int pos = base + item;
         const int i = find_instance(b.scan, beg, end, pos);
         const InstView& v = b.views[i];
-        const long long round = v.ctr->round;
-        const int seg = seglist_of(v, (int)(round & 1))[pos - b.scan[i]];
+        const int ch = pos - b.scan[i];
         int exact = 0;
-        const int r = relax_segment<D, RECOMP, false>(v, seg, round, &exact);
+        const int r = relax_chunk<D, FMT, false>(v, ch << 5, v.ctr->ncur - (ch << 5), v.ctr->round, &exact);
         if ((threadIdx.x & 31) == 0 && r)
             atomicAdd((unsigned long long*)&v.ctr->relaxed, (unsigned long long)r);
     }
@@ -213,15 +230,33 @@ template <int D>
 __global__ void __launch_bounds__(256, 4) k_b_propagate(BatchDev b, int g) {
     const int beg = b.gbeg[g], end = b.gbeg[g + 1];
     if (beg >= end) return;
-    const int base = b.scan[beg], total = b.scan[end] - base;
+    const int base = b.scan_chg[beg], total = b.scan_chg[end] - base;
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < total; item += nwarps) {
         const int pos = base + item;
-        const int i = find_instance(b.scan, beg, end, pos);
+        const int i = find_instance(b.scan_chg, beg, end, pos);
         const InstView& v = b.views[i];
-        const int par = (int)((v.ctr->round + 1) & 1);
-        propagate_cell<D>(v, v.chg[pos - b.scan[i]], par, true);
+        propagate_cell<D>(v, v.chg[pos - b.scan_chg[i]], true);
+    }
+}
+
+// Compaction of every unfinished instance (block per 256-word chunk) and the
+// refresh of the window tables around every changed cell.
+__global__ void __launch_bounds__(256) k_b_compact(BatchDev b) {
+    const int n = b.n;
+    const int total = b.scan_cmp[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int i = find_instance(b.scan_cmp, 0, n, item);
+        const InstView& v = b.views[i];
+        const int nwords = (int)((v.g.C + 31) >> 5);
+        compact_words(v, (item - b.scan_cmp[i]) << 8, nwords);
+    }
+    const int tchg = b.scan_chg[n];
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < tchg; item += gridDim.x * blockDim.x) {
+        const int i = find_instance(b.scan_chg, 0, n, item);
+        const InstView& v = b.views[i];
+        refresh_tables(v, v.chg[item - b.scan_chg[i]]);
     }
 }
 
@@ -255,7 +290,7 @@ Engine::~Engine() {
 
 size_t Engine::state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, bool stage_V) const {
     const size_t C = (size_t)a->g.C, U = (size_t)a->g.U, S = (C + 31) / 32;
-    size_t o = r256(sizeof(Counters)) + 2 * r256(8 * C) + r256(C) + 3 * r256(4 * S) + r256(4 * C) +
+    size_t o = r256(sizeof(Counters)) + 4 * r256(8 * C) + r256(C) + r256(4 * S) + 2 * r256(4 * C) +
                r256(8 * C * U);
     if (stage_G) o += r256(8 * C * U);
     if (stage_T) o += r256(8 * C) + r256(C) + r256(C);   // terminal or target, plus avoid
@@ -264,7 +299,7 @@ size_t Engine::state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, 
 }
 
 static int group_of(const bf_abstraction* a) {
-    return (a->g.D - 1) * 2 + (a->mode == BF_MODE_RECOMPUTE ? 1 : 0);
+    return (a->g.D - 1) * 3 + a->box_fmt;
 }
 
 int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* target,
@@ -287,10 +322,11 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
     const size_t o_ctr = o;  o += r256(sizeof(Counters));
     const size_t o_vk = o;   o += r256(8 * (size_t)C);
     const size_t o_vn = o;   o += r256(8 * (size_t)C);
+    const size_t o_m2 = o;   o += r256(8 * (size_t)C);
+    const size_t o_m3 = o;   o += r256(8 * (size_t)C);
     const size_t o_mu = o;   o += r256((size_t)C);
     const size_t o_fb = o;   o += r256(4 * (size_t)S);
-    const size_t o_l0 = o;   o += r256(4 * (size_t)S);
-    const size_t o_l1 = o;   o += r256(4 * (size_t)S);
+    const size_t o_cl = o;   o += r256(4 * (size_t)C);
     const size_t o_chg = o;  o += r256(4 * (size_t)C);
     const size_t o_gi = o;   o += r256(8 * (size_t)C * U);
     const size_t o_sg = o;   o += sG ? r256(8 * (size_t)C * U) : 0;
@@ -308,26 +344,15 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
     s->cap = (max_iters > 0 && max_iters < C) ? max_iters : C;
     InstView& v = s->view;
     memset(&v, 0, sizeof v);
-    v.g = a->g;
-    v.dd.kind = a->dyn.kind;
-    v.dd.substeps = a->dyn.rk4_substeps;
-    v.dd.udim = a->udim;
-    v.dd.tau = a->tau;
-    for (int i = 0; i < 8; ++i) v.dd.p[i] = a->dyn.param[i];
-    for (int d = 0; d < a->g.D; ++d) {
-        v.dd.glo[d] = a->glo[d];
-        v.dd.eta[d] = (a->ghi[d] - a->glo[d]) / (double)a->g.n[d];
-    }
-    v.boxes = a->d_boxes;
-    v.inputs = a->d_inputs;
-    v.pred = a->d_pred;
+    view_from_abs(v, a);
     v.ctr = reinterpret_cast<Counters*>(m + o_ctr);
     v.Vkey = reinterpret_cast<long long*>(m + o_vk);
     v.Vnew = reinterpret_cast<long long*>(m + o_vn);
+    v.M2 = reinterpret_cast<long long*>(m + o_m2);
+    v.M3 = reinterpret_cast<long long*>(m + o_m3);
     v.mu = m + o_mu;
     v.fbits = reinterpret_cast<unsigned*>(m + o_fb);
-    v.seglist0 = reinterpret_cast<int*>(m + o_l0);
-    v.seglist1 = reinterpret_cast<int*>(m + o_l1);
+    v.cells = reinterpret_cast<int*>(m + o_cl);
     v.chg = reinterpret_cast<int*>(m + o_chg);
     v.Gint = reinterpret_cast<const double*>(m + o_gi);
     // inputs
@@ -361,6 +386,7 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
     const int nb = blocks_for(C);
     k_b_costs<<<nb, 256, 0, st_>>>(C, U, dG, dAv, const_cast<double*>(v.Gint), v.ctr);
     k_b_values<<<nb, 256, 0, st_>>>(C, dT, dTg, dAv, v.Vkey, v.Vnew, v.mu, v.chg, v.ctr);
+    k_b_tables<<<nb, 256, 0, st_>>>(v);
     const int pb = n_sms() * 4;
     switch (a->g.D) {
         case 1: k_b_propagate_init<1><<<pb, 256, 0, st_>>>(v); break;
@@ -368,7 +394,7 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
         case 3: k_b_propagate_init<3><<<pb, 256, 0, st_>>>(v); break;
         default: k_b_propagate_init<4><<<pb, 256, 0, st_>>>(v); break;
     }
-    k_b_start<<<1, 1, 0, st_>>>(v.ctr);
+    k_b_compact_init<<<blocks_for(S), 256, 0, st_>>>(v, S);
     BF_CUDA(cudaGetLastError());
     insts_.push_back(s);
     if (out) *out = s;
@@ -388,21 +414,20 @@ int Engine::rebuild() {
     const int n = (int)insts_.size();
     memset(&dev_, 0, sizeof dev_);
     dev_.n = n;
-    // groups
+    // groups (same dimension and box format)
     int ng = 0;
     for (int i = 0; i < n; ++i) {
         const int g = insts_[i]->group;
-        if (ng == 0 || group_D_[ng - 1] * 2 + group_rc_[ng - 1] - 2 != g) {
-            group_D_[ng] = g / 2 + 1;
-            group_rc_[ng] = g % 2;
+        if (ng == 0 || (group_D_[ng - 1] - 1) * 3 + group_fmt_[ng - 1] != g) {
+            group_D_[ng] = g / 3 + 1;
+            group_fmt_[ng] = g % 3;
             dev_.gbeg[ng] = i;
             ++ng;
         }
     }
     dev_.ngroups = ng;
     dev_.gbeg[ng] = n;
-    const size_t need = r256(sizeof(InstView) * std::max(n, 1)) + r256(4 * (size_t)(n + 1)) +
-                        r256(4 * kMaxGroups) + r256(4);
+    const size_t need = r256(sizeof(InstView) * std::max(n, 1)) + 3 * r256(4 * (size_t)(n + 1)) + r256(4);
     if (need > dev_mem_bytes_) {
         if (dev_mem_) BF_CUDA(cudaFreeAsync(dev_mem_, st_));
         dev_mem_ = nullptr;
@@ -414,8 +439,10 @@ int Engine::rebuild() {
     m += r256(sizeof(InstView) * std::max(n, 1));
     dev_.scan = reinterpret_cast<int*>(m);
     m += r256(4 * (size_t)(n + 1));
-    dev_.totals = reinterpret_cast<int*>(m);
-    m += r256(4 * kMaxGroups);
+    dev_.scan_chg = reinterpret_cast<int*>(m);
+    m += r256(4 * (size_t)(n + 1));
+    dev_.scan_cmp = reinterpret_cast<int*>(m);
+    m += r256(4 * (size_t)(n + 1));
     dev_.active = reinterpret_cast<int*>(m);
     host_views_.resize(n);
     for (int i = 0; i < n; ++i) host_views_[i] = insts_[i]->view;
@@ -428,14 +455,18 @@ int Engine::rebuild() {
     if (!relax_blocks_) {
         relax_blocks_ = n_sms() * 4;
         prop_blocks_ = n_sms() * 4;
+        compact_blocks_ = n_sms() * 8;
     }
     return BF_OK;
 }
 
 template <int D>
-static void launch_relax(const BatchDev& b, int g, int rc, int blocks, cudaStream_t st) {
-    if (rc) k_b_relax<D, true><<<blocks / 2, 256, 0, st>>>(b, g);
-    else k_b_relax<D, false><<<blocks, 256, 0, st>>>(b, g);
+static void launch_relax(const BatchDev& b, int g, int fmt, int blocks, cudaStream_t st) {
+    switch (fmt) {
+        case kBoxCompact: k_b_relax<D, kBoxCompact><<<blocks, 256, 0, st>>>(b, g); break;
+        case kBoxRecompute: k_b_relax<D, kBoxRecompute><<<blocks / 2, 256, 0, st>>>(b, g); break;
+        default: k_b_relax<D, kBoxWide><<<blocks, 256, 0, st>>>(b, g); break;
+    }
 }
 
 template <int D>
@@ -446,10 +477,10 @@ static void launch_prop(const BatchDev& b, int g, int blocks, cudaStream_t st) {
 void Engine::launch_pass(cudaGraphConditionalHandle h, int use_graph) {
     for (int g = 0; g < dev_.ngroups; ++g) {
         switch (group_D_[g]) {
-            case 1: launch_relax<1>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
-            case 2: launch_relax<2>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
-            case 3: launch_relax<3>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
-            default: launch_relax<4>(dev_, g, group_rc_[g], relax_blocks_, st_); break;
+            case 1: launch_relax<1>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
+            case 2: launch_relax<2>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
+            case 3: launch_relax<3>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
+            default: launch_relax<4>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
         }
     }
     k_b_plan<<<1, 1024, 0, st_>>>(dev_, 1, h, use_graph);
@@ -461,6 +492,7 @@ void Engine::launch_pass(cudaGraphConditionalHandle h, int use_graph) {
             default: launch_prop<4>(dev_, g, prop_blocks_, st_); break;
         }
     }
+    k_b_compact<<<compact_blocks_, 256, 0, st_>>>(dev_);
     k_b_plan<<<1, 1024, 0, st_>>>(dev_, 2, h, use_graph);
 }
 

@@ -23,13 +23,14 @@ namespace bfb {
 using bfk::Counters;
 using bfk::InstView;
 
-constexpr int kMaxGroups = 8;   // D in 1..4 x {stored, recompute}
+constexpr int kMaxGroups = 12;  // D in 1..4 x {wide, compact, recompute} boxes
 
 // Device-side description of one batch (rebuilt when the instance set changes).
 struct BatchDev {
     InstView* views;    // [n], ordered by group
-    int* scan;          // [n + 1] exclusive prefix of the per-instance work counts
-    int* totals;        // [kMaxGroups] work items per group
+    int* scan;          // [n + 1] exclusive prefix of the per-instance relax chunks
+    int* scan_chg;      // [n + 1] exclusive prefix of the changed cells
+    int* scan_cmp;      // [n + 1] exclusive prefix of the 256-word compaction chunks
     int* active;        // [1] unfinished instances
     int n;
     int ngroups;
@@ -89,8 +90,8 @@ private:
     BatchDev dev_{};
     void* dev_mem_ = nullptr;
     size_t dev_mem_bytes_ = 0;
-    int relax_blocks_ = 0, prop_blocks_ = 0;
-    int group_D_[kMaxGroups] = {}, group_rc_[kMaxGroups] = {};
+    int relax_blocks_ = 0, prop_blocks_ = 0, compact_blocks_ = 0;
+    int group_D_[kMaxGroups] = {}, group_fmt_[kMaxGroups] = {};
 };
 
 }  // namespace bfb

@@ -19,6 +19,11 @@
 namespace bfk {
 
 constexpr int16_t kBlocked = -32768;
+
+// storage formats of an abstraction's boxes
+constexpr int kBoxWide = 0;      // int16 absolute records [U][C] (4*D bytes)
+constexpr int kBoxCompact = 1;   // int8 relative records [U][C] (4 bytes for D <= 2, else 8)
+constexpr int kBoxRecompute = 2; // not stored: regenerated from the dynamics
 constexpr long long kKeyInf = 0x7FF0000000000000LL;   // key(+inf) == bits(+inf)
 constexpr long long kKeyMin = (long long)0x8000000000000000ULL;
 constexpr unsigned char kHandover = 0xFF;
@@ -168,8 +173,9 @@ struct bf_abstraction {
     double tau;
     int udim;
     double* d_inputs;         // [U][udim]
-    // stored mode: boxes [U][C] x (4*D bytes)
+    // stored mode: boxes [U][C], wide (4*D bytes) or compact records
     void* d_boxes;
+    int box_fmt;              // bfk::kBoxWide / kBoxCompact / kBoxRecompute
     // predecessor index [C][2*D] int16 offsets (x = y + off), empty: lo0 > hi0
     short* d_pred;
     size_t bytes;

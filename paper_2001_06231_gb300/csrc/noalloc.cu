@@ -53,7 +53,7 @@ size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Carve the scratch array; returns the bytes needed (may exceed the array).
 struct Layout {
-    size_t ctr, vkey, vnew, fbits, list0, list1, chg, gint, total;
+    size_t ctr, vkey, vnew, m2, m3, fbits, cells, chg, gint, total;
 };
 
 Layout plan(long long C, int U) {
@@ -63,9 +63,10 @@ Layout plan(long long C, int U) {
     L.ctr = o;   o += round256(sizeof(Counters));
     L.vkey = o;  o += round256(8 * (size_t)C);
     L.vnew = o;  o += round256(8 * (size_t)C);
+    L.m2 = o;    o += round256(8 * (size_t)C);
+    L.m3 = o;    o += round256(8 * (size_t)C);
     L.fbits = o; o += round256(4 * (size_t)S);
-    L.list0 = o; o += round256(4 * (size_t)S);
-    L.list1 = o; o += round256(4 * (size_t)S);
+    L.cells = o; o += round256(4 * (size_t)C);
     L.chg = o;   o += round256(4 * (size_t)C);
     L.gint = o;  o += round256(8 * (size_t)C * U);
     L.total = o;
@@ -130,45 +131,53 @@ __global__ void k_na_values(long long C, const double* __restrict__ terminal,
     if (bad) atomicOr(&ctr->err, 1);
 }
 
-template <int D, bool RECOMP>
-__global__ void __launch_bounds__(256, RECOMP ? 2 : 4) k_na_relax(InstView v) {
+__global__ void k_na_tables(InstView v) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < v.g.C;
+         c += (long long)gridDim.x * blockDim.x)
+        table_entry(v, c);
+}
+
+template <int D, int FMT>
+__global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_na_relax(InstView v) {
     Counters* k = v.ctr;
     if (k->done) return;
     const long long round = k->round;
-    const int par = (int)(round & 1);
-    const int nseg = k->nseg[par];
-    const int* list = seglist_of(v, par);
+    const int ncur = k->ncur;
+    const int nchunks = (ncur + 31) >> 5;
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     long long relaxed = 0;
     int exact = 0;
-    for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < nseg; s += nwarps)
-        relaxed += relax_segment<D, RECOMP, false>(v, list[s], round, &exact);
+    for (int ch = blockIdx.x * wpb + (threadIdx.x >> 5); ch < nchunks; ch += nwarps)
+        relaxed += relax_chunk<D, FMT, false>(v, ch << 5, ncur - (ch << 5), round, &exact);
     if ((threadIdx.x & 31) == 0 && relaxed)
         atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, 4) k_na_propagate(InstView v, int init) {
+__global__ void __launch_bounds__(256, 4) k_na_propagate(InstView v, int commit) {
     Counters* k = v.ctr;
     if (k->done) return;
-    const int par = init ? 0 : (int)((k->round + 1) & 1);
     const int nchg = k->nchg;
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
-        propagate_cell<D>(v, v.chg[i], par, !init);
+        propagate_cell<D>(v, v.chg[i], commit != 0);
+}
+
+__global__ void __launch_bounds__(256) k_na_compact(InstView v, long long nwords, int init) {
+    Counters* k = v.ctr;
+    if (k->done) return;
+    for (long long wb = (long long)blockIdx.x * blockDim.x; wb < nwords; wb += (long long)gridDim.x * blockDim.x)
+        compact_words(v, (int)wb, (int)nwords);
+    if (!init) {
+        const int nchg = k->nchg;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchg; i += gridDim.x * blockDim.x)
+            refresh_tables(v, v.chg[i]);
+    }
     if (last_block_done(&k->blocks_done)) {
-        if (init) {
-            k->nchg = 0;
-            const bool cont = k->err == 0 && k->nseg[0] > 0 && k->cap > 0;
-            if (!cont) {
-                k->done = 1;
-                k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
-            }
-        } else {
-            finish_pass(v);
-        }
+        if (init) start_loop(v);
+        else finish_pass(v);
     }
 }
 
@@ -192,20 +201,30 @@ int wave(K kernel) {
     return (per_sm < 1 ? 1 : per_sm) * sms();
 }
 
+template <int D, int FMT>
+void launch_relax(const InstView& v, int blocks, cudaStream_t st) {
+    k_na_relax<D, FMT><<<blocks, 256, 0, st>>>(v);
+}
+
 template <int D>
 int run(const bf_abstraction* a, const InstView& v, const double* G, const unsigned char* target,
         const unsigned char* avoid, const double* terminal, double* V, cudaStream_t st,
         Counters* hc_out) {
     const long long C = a->g.C;
     const int U = a->g.U;
-    const bool rc = a->mode == BF_MODE_RECOMPUTE;
+    const long long S = (C + 31) / 32;
+    const int fmt = a->box_fmt;
     const int nb = (int)(((C + 255) / 256) < (long long)sms() * 8 ? (C + 255) / 256 : (long long)sms() * 8);
-    const int rb = rc ? wave(k_na_relax<D, true>) : wave(k_na_relax<D, false>);
+    const int cb = (int)(((S + 255) / 256) < (long long)sms() * 8 ? (S + 255) / 256 : (long long)sms() * 8);
+    const int rb = fmt == kBoxRecompute ? wave(k_na_relax<D, kBoxRecompute>)
+                 : fmt == kBoxCompact ? wave(k_na_relax<D, kBoxCompact>) : wave(k_na_relax<D, kBoxWide>);
     const int pb = wave(k_na_propagate<D>);
     k_na_costs<<<nb, 256, 0, st>>>(C, U, G, avoid, const_cast<double*>(v.Gint), v.ctr);
     k_na_values<<<nb, 256, 0, st>>>(C, terminal, terminal ? nullptr : target, avoid, v.Vkey, v.Vnew, v.mu,
                                     v.chg, v.ctr);
-    k_na_propagate<D><<<pb, 256, 0, st>>>(v, 1);
+    k_na_tables<<<nb, 256, 0, st>>>(v);
+    k_na_propagate<D><<<pb, 256, 0, st>>>(v, 0);
+    k_na_compact<<<cb, 256, 0, st>>>(v, S, 1);
     BF_CUDA(cudaGetLastError());
     Counters hc;
     for (;;) {
@@ -213,9 +232,13 @@ int run(const bf_abstraction* a, const InstView& v, const double* G, const unsig
         BF_CUDA(cudaStreamSynchronize(st));
         if (hc.done) break;
         for (int i = 0; i < kPassesPerCheck; ++i) {
-            if (rc) k_na_relax<D, true><<<rb, 256, 0, st>>>(v);
-            else k_na_relax<D, false><<<rb, 256, 0, st>>>(v);
-            k_na_propagate<D><<<pb, 256, 0, st>>>(v, 0);
+            switch (fmt) {
+                case kBoxCompact: launch_relax<D, kBoxCompact>(v, rb, st); break;
+                case kBoxRecompute: launch_relax<D, kBoxRecompute>(v, rb, st); break;
+                default: launch_relax<D, kBoxWide>(v, rb, st); break;
+            }
+            k_na_propagate<D><<<pb, 256, 0, st>>>(v, 1);
+            k_na_compact<<<cb, 256, 0, st>>>(v, S, 0);
         }
         BF_CUDA(cudaGetLastError());
     }
@@ -266,31 +289,21 @@ extern "C" int bf_solve_noalloc(const bf_abstraction* a, const double* G, const 
     cudaStream_t st = (cudaStream_t)stream;
     InstView v;
     memset(&v, 0, sizeof v);
-    v.g = a->g;
-    v.dd.kind = a->dyn.kind;
-    v.dd.substeps = a->dyn.rk4_substeps;
-    v.dd.udim = a->udim;
-    v.dd.tau = a->tau;
-    for (int i = 0; i < 8; ++i) v.dd.p[i] = a->dyn.param[i];
-    for (int d = 0; d < a->g.D; ++d) {
-        v.dd.glo[d] = a->glo[d];
-        v.dd.eta[d] = (a->ghi[d] - a->glo[d]) / (double)a->g.n[d];
-    }
-    v.boxes = a->d_boxes;
-    v.inputs = a->d_inputs;
-    v.pred = a->d_pred;
+    view_from_abs(v, a);
     v.Gint = reinterpret_cast<const double*>(s + L.gint);
     v.Vkey = reinterpret_cast<long long*>(s + L.vkey);
     v.Vnew = reinterpret_cast<long long*>(s + L.vnew);
+    v.M2 = reinterpret_cast<long long*>(s + L.m2);
+    v.M3 = reinterpret_cast<long long*>(s + L.m3);
     v.mu = mu;
     v.fbits = reinterpret_cast<unsigned*>(s + L.fbits);
-    v.seglist0 = reinterpret_cast<int*>(s + L.list0);
-    v.seglist1 = reinterpret_cast<int*>(s + L.list1);
+    v.cells = reinterpret_cast<int*>(s + L.cells);
     v.chg = reinterpret_cast<int*>(s + L.chg);
     v.ctr = reinterpret_cast<Counters*>(s + L.ctr);
     long long cap = C;
     if (max_iters > 0 && max_iters < cap) cap = max_iters;
-    // what must start at zero: the counters and the frontier bitmap
+    // what must start at zero: the counters (including the last-block counter
+    // of the compaction) and the frontier bitmap
     k_na_counters<<<1, 1, 0, st>>>(v.ctr, cap);
     BF_CUDA(cudaMemsetAsync(v.fbits, 0, 4 * (size_t)((C + 31) / 32), st));
     Counters hc;

@@ -302,7 +302,7 @@ extern "C" int bf_serve_submit(bf_server* s, const bf_request* q, uint64_t* id) 
         r->abs = q->abs;
         int64_t nc = 0;
         int32_t nu = 0;
-        abs_info(q->abs, &nc, &nu, nullptr, nullptr, nullptr);
+        abs_info(q->abs, &nc, &nu, nullptr, nullptr, nullptr, nullptr);
         C = nc;
         U = nu;
     } else {

@@ -1,22 +1,18 @@
 // solve.cu -- bf_solve: Algorithm 1 (generalized Bellman-Ford-Yen, Sec. IV-A)
 // on one abstraction, on one GPU.
 //
-// Device state per solve (workspace, cached in the abstraction handle):
-//   Vkey, Vnew  int64 [C]   values as order-preserving keys (bf_internal.cuh)
-//   mu          uint8 [C]
-//   fbits       u32 [S]     upcoming frontier, one bit per cell; word s covers
-//                           the segment of cells 32s .. 32s+31
-//   seglist     i32 [2][S]  active segments of the current / next frontier
-//   chg         i32 [C]     cells changed in the current pass
-//   Gint        f64 [U][C]  running cost, input-major (coalesced per input),
-//                           +inf on avoid cells; -0 read as +0
-// Frontiers (F1 / F2 of Algorithm 1) are the bitmap plus the compacted
-// segment list; the grid is never scanned whole.
+// Device state per solve (workspace, cached in the abstraction handle): the
+// InstView arrays of solve_core.cuh (values as int64 keys, window-max tables,
+// frontier bitmap and compacted frontier list, changed list) plus
+//   Gint   f64 [U][C]  running cost, input-major (coalesced per input),
+//                      +inf on avoid cells; -0 read as +0.
 //
 // Round driver: the passes run inside one CUDA graph whose body (relax ->
-// propagate) sits in a conditional WHILE node; the last block of propagate
-// evaluates "F1 != empty and i < cap" on the device and sets the condition,
-// so a whole solve is one graph launch with no host round trip per pass.
+// propagate -> compact) sits in a conditional WHILE node; the last block of
+// compact evaluates "F1 != empty and i < cap" on the device and sets the
+// condition, so a whole solve is one graph launch with no host round trip per
+// pass.  The set-up (lines 1-10 of Algorithm 1) and the output conversion are
+// ordinary launches on the caller's stream.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -32,12 +28,14 @@ struct bf_solve_ws {
     long long C = 0;
     int U = 0, D = 0;
     int device = 0;
-    long long nseg_total = 0;
+    long long nwords = 0;
     long long* Vkey = nullptr;
     long long* Vnew = nullptr;
+    long long* M2 = nullptr;
+    long long* M3 = nullptr;
     unsigned char* mu = nullptr;
     unsigned* fbits = nullptr;
-    int* seglist = nullptr;       // 2 * nseg_total
+    int* cells = nullptr;
     int* chg = nullptr;
     double* Gint = nullptr;
     Counters* ctr = nullptr;
@@ -53,7 +51,7 @@ struct bf_solve_ws {
     // graph of the pass loop
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
-    int relax_blocks = 0, prop_blocks = 0;
+    int relax_blocks = 0, prop_blocks = 0, compact_blocks = 0;
     std::mutex mtx;
 };
 
@@ -61,10 +59,10 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     if (!w) return;
     if (w->exec) cudaGraphExecDestroy(w->exec);
     if (w->graph) cudaGraphDestroy(w->graph);
-    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->mu); cudaFree(w->fbits);
-    cudaFree(w->seglist); cudaFree(w->chg); cudaFree(w->Gint);
-    cudaFree(w->ctr); cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt);
-    cudaFree(w->stage_avoid); cudaFree(w->stage_V); cudaFree(w->trace); cudaFree(w->stamp);
+    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->M2); cudaFree(w->M3); cudaFree(w->mu);
+    cudaFree(w->fbits); cudaFree(w->cells); cudaFree(w->chg); cudaFree(w->Gint); cudaFree(w->ctr);
+    cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt); cudaFree(w->stage_avoid);
+    cudaFree(w->stage_V); cudaFree(w->trace); cudaFree(w->stamp);
     delete w;
 }
 
@@ -100,8 +98,8 @@ __global__ void k_init_costs(long long C, int U, const double* __restrict__ G,
 }
 
 // Lines 1-9 of Algorithm 1: W = terminal cost (0 on target, +inf elsewhere,
-// or the caller's array), mu = U (hand over), and the cells with finite W go
-// to the changed list so that the first propagate builds F1 from their preds.
+// or the caller's array), mu = U (hand over); the cells with finite W go to
+// the changed list so that the first propagate builds F1 from their preds.
 __global__ void k_init_values(long long C, const double* __restrict__ terminal,
                               const unsigned char* __restrict__ target,
                               const unsigned char* __restrict__ avoid, long long* Vkey,
@@ -136,6 +134,12 @@ __global__ void k_init_values(long long C, const double* __restrict__ terminal,
     if (bad) atomicOr(&ctr->err, 1);
 }
 
+__global__ void k_init_tables(InstView v) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < v.g.C;
+         c += (long long)gridDim.x * blockDim.x)
+        table_entry(v, c);
+}
+
 __global__ void k_init_counters(Counters* ctr, long long cap) {
     memset(ctr, 0, sizeof(Counters));
     ctr->cap = cap;
@@ -144,56 +148,57 @@ __global__ void k_init_counters(Counters* ctr, long long cap) {
 // ---------------------------------------------------------------------------
 // pass kernels
 // ---------------------------------------------------------------------------
-template <int D, bool RECOMP, bool COUNT>
-__global__ void __launch_bounds__(256, RECOMP ? 2 : 4) k_relax(InstView v) {
+template <int D, int FMT, bool COUNT>
+__global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_relax(InstView v) {
     Counters* k = v.ctr;
     if (k->done) return;
     const long long round = k->round;
-    const int par = (int)(round & 1);
-    const int nseg = k->nseg[par];
-    const int* list = seglist_of(v, par);
+    const int ncur = k->ncur;
+    const int nchunks = (ncur + 31) >> 5;
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     long long relaxed = 0;
     int exact = 0;
-    for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < nseg; s += nwarps)
-        relaxed += relax_segment<D, RECOMP, COUNT>(v, list[s], round, &exact);
+    for (int ch = blockIdx.x * wpb + (threadIdx.x >> 5); ch < nchunks; ch += nwarps)
+        relaxed += relax_chunk<D, FMT, COUNT>(v, ch << 5, ncur - (ch << 5), round, &exact);
     if ((threadIdx.x & 31) == 0) {
         if (relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
         if (COUNT && exact) atomicAdd((unsigned long long*)&k->exact, (unsigned long long)exact);
     }
 }
 
-// Propagate (warp per changed cell).  The last block to finish closes
-// the pass: after the initial propagate it only decides whether to loop;
-// after a pass it runs finish_pass.  With a graph it sets the WHILE
-// condition.
+// Propagate (warp per changed cell): commit W and set F2's bits.
 template <int D>
-__global__ void __launch_bounds__(256, 4) k_propagate(InstView v, int init, cudaGraphConditionalHandle h,
-                                                   int use_graph) {
+__global__ void __launch_bounds__(256, 4) k_propagate(InstView v, int commit) {
+    Counters* k = v.ctr;
+    if (k->done) return;
+    const int nchg = k->nchg;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
+        propagate_cell<D>(v, v.chg[i], commit != 0);
+}
+
+// Compact F2 into the next frontier list, refresh the window tables around
+// the changed cells, and (last block) close the pass or, after the set-up,
+// decide whether to loop.  With a graph the last block sets the WHILE
+// condition.
+__global__ void __launch_bounds__(256) k_compact(InstView v, long long nwords, int init,
+                                                 cudaGraphConditionalHandle h, int use_graph) {
     Counters* k = v.ctr;
     if (k->done) {
         if (use_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0);
         return;
     }
-    const int par = init ? 0 : (int)((k->round + 1) & 1);
-    const int nchg = k->nchg;
-    const int wpb = blockDim.x >> 5;
-    const int nwarps = gridDim.x * wpb;
-    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
-        propagate_cell<D>(v, v.chg[i], par, !init);
+    for (long long wb = (long long)blockIdx.x * blockDim.x; wb < nwords; wb += (long long)gridDim.x * blockDim.x)
+        compact_words(v, (int)wb, (int)nwords);
+    if (!init) {
+        const int nchg = k->nchg;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchg; i += gridDim.x * blockDim.x)
+            refresh_tables(v, v.chg[i]);
+    }
     if (last_block_done(&k->blocks_done)) {
-        int cont;
-        if (init) {
-            k->nchg = 0;
-            cont = (k->err == 0 && k->nseg[0] > 0 && k->cap > 0) ? 1 : 0;
-            if (!cont) {
-                k->done = 1;
-                k->status = k->nseg[0] == 0 ? BF_CONVERGED : BF_ITER_CAP;
-            }
-        } else {
-            cont = finish_pass(v);
-        }
+        const int cont = init ? start_loop(v) : finish_pass(v);
         if (use_graph) cudaGraphSetConditional(h, cont);
     }
 }
@@ -242,15 +247,17 @@ static int ws_get(const bf_abstraction* a, bf_solve_ws** out) {
     w->U = a->g.U;
     w->D = a->g.D;
     cudaGetDevice(&w->device);
-    w->nseg_total = (a->g.C + 31) / 32;
-    const long long C = w->C, S = w->nseg_total;
+    w->nwords = (a->g.C + 31) / 32;
+    const long long C = w->C, S = w->nwords;
     cudaError_t e = cudaSuccess;
     auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
     A((void**)&w->Vkey, 8 * C);
     A((void**)&w->Vnew, 8 * C);
+    A((void**)&w->M2, 8 * C);
+    A((void**)&w->M3, 8 * C);
     A((void**)&w->mu, C);
     A((void**)&w->fbits, 4 * S);
-    A((void**)&w->seglist, 8 * S);
+    A((void**)&w->cells, 4 * C);
     A((void**)&w->chg, 4 * C);
     A((void**)&w->Gint, 8 * C * w->U);
     A((void**)&w->ctr, sizeof(Counters));
@@ -263,26 +270,15 @@ static int ws_get(const bf_abstraction* a, bf_solve_ws** out) {
 static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     InstView v;
     memset(&v, 0, sizeof v);
-    v.g = a->g;
-    v.dd.kind = a->dyn.kind;
-    v.dd.substeps = a->dyn.rk4_substeps;
-    v.dd.udim = a->udim;
-    v.dd.tau = a->tau;
-    for (int i = 0; i < 8; ++i) v.dd.p[i] = a->dyn.param[i];
-    for (int d = 0; d < a->g.D; ++d) {
-        v.dd.glo[d] = a->glo[d];
-        v.dd.eta[d] = (a->ghi[d] - a->glo[d]) / (double)a->g.n[d];
-    }
-    v.boxes = a->d_boxes;
-    v.inputs = a->d_inputs;
-    v.pred = a->d_pred;
+    view_from_abs(v, a);
     v.Gint = w->Gint;
     v.Vkey = w->Vkey;
     v.Vnew = w->Vnew;
+    v.M2 = w->M2;
+    v.M3 = w->M3;
     v.mu = w->mu;
     v.fbits = w->fbits;
-    v.seglist0 = w->seglist;
-    v.seglist1 = w->seglist + w->nseg_total;
+    v.cells = w->cells;
     v.chg = w->chg;
     v.ctr = w->ctr;
     v.trace = w->trace;
@@ -290,24 +286,31 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     return v;
 }
 
-// Launch one pass (relax, propagate, finish) of the given dimension.  With
-// timing events, the relax and propagate launches are each bracketed.
+// Launch one pass (relax, propagate, compact).  With timing events, the relax
+// and propagate launches are each bracketed.
 struct PassTimers {
     cudaEvent_t e[4];
 };
+
+template <int D, int FMT>
+static void launch_relax(bf_solve_ws* w, const InstView& v, cudaStream_t st, bool count) {
+    if (count) k_relax<D, FMT, true><<<w->relax_blocks, 256, 0, st>>>(v);
+    else k_relax<D, FMT, false><<<w->relax_blocks, 256, 0, st>>>(v);
+}
 
 template <int D>
 static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
                         cudaGraphConditionalHandle h, int use_graph, bool count, PassTimers* tm) {
     if (tm) cudaEventRecord(tm->e[0], st);
-    const bool rc = a->mode == BF_MODE_RECOMPUTE;
-    if (rc && count) k_relax<D, true, true><<<w->relax_blocks, 256, 0, st>>>(v);
-    else if (rc) k_relax<D, true, false><<<w->relax_blocks, 256, 0, st>>>(v);
-    else if (count) k_relax<D, false, true><<<w->relax_blocks, 256, 0, st>>>(v);
-    else k_relax<D, false, false><<<w->relax_blocks, 256, 0, st>>>(v);
+    switch (a->box_fmt) {
+        case kBoxCompact: launch_relax<D, kBoxCompact>(w, v, st, count); break;
+        case kBoxRecompute: launch_relax<D, kBoxRecompute>(w, v, st, count); break;
+        default: launch_relax<D, kBoxWide>(w, v, st, count); break;
+    }
     if (tm) { cudaEventRecord(tm->e[1], st); cudaEventRecord(tm->e[2], st); }
-    k_propagate<D><<<w->prop_blocks, 256, 0, st>>>(v, 0, h, use_graph);
+    k_propagate<D><<<w->prop_blocks, 256, 0, st>>>(v, 1);
     if (tm) cudaEventRecord(tm->e[3], st);
+    k_compact<<<w->compact_blocks, 256, 0, st>>>(v, w->nwords, 0, h, use_graph);
 }
 
 static void launch_pass_any(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
@@ -321,24 +324,30 @@ static void launch_pass_any(const bf_abstraction* a, bf_solve_ws* w, const InstV
     }
 }
 
-static void launch_init_propagate(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st) {
+// Set-up tail: the first propagate (pred of the finite cells) and compaction.
+static void launch_setup_frontier(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st) {
     switch (a->g.D) {
-        case 1: k_propagate<1><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
-        case 2: k_propagate<2><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
-        case 3: k_propagate<3><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
-        default: k_propagate<4><<<w->prop_blocks, 256, 0, st>>>(v, 1, 0, 0); break;
+        case 1: k_propagate<1><<<w->prop_blocks, 256, 0, st>>>(v, 0); break;
+        case 2: k_propagate<2><<<w->prop_blocks, 256, 0, st>>>(v, 0); break;
+        case 3: k_propagate<3><<<w->prop_blocks, 256, 0, st>>>(v, 0); break;
+        default: k_propagate<4><<<w->prop_blocks, 256, 0, st>>>(v, 0); break;
     }
+    k_compact<<<w->compact_blocks, 256, 0, st>>>(v, w->nwords, 1, 0, 0);
 }
 
 template <int D>
 static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
-    w->relax_blocks = a->mode == BF_MODE_RECOMPUTE ? full_wave(k_relax<D, true, false>, 256)
-                                                   : full_wave(k_relax<D, false, false>, 256);
+    switch (a->box_fmt) {
+        case kBoxCompact: w->relax_blocks = full_wave(k_relax<D, kBoxCompact, false>, 256); break;
+        case kBoxRecompute: w->relax_blocks = full_wave(k_relax<D, kBoxRecompute, false>, 256); break;
+        default: w->relax_blocks = full_wave(k_relax<D, kBoxWide, false>, 256); break;
+    }
     w->prop_blocks = full_wave(k_propagate<D>, 256);
+    w->compact_blocks = blocks_for(w->nwords, 256);
 }
 
 // Build (once per workspace) the graph: [loop condition] -> WHILE { pass }.
-static int ws_graph(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
+static int ws_graph(const bf_abstraction* a, bf_solve_ws* w) {
     if (w->exec) return BF_OK;
     cudaGraph_t graph;
     BF_CUDA(cudaGraphCreate(&graph, 0));
@@ -379,7 +388,6 @@ static int ws_graph(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
     BF_CUDA(e);
     BF_CUDA(cudaGraphInstantiate(&w->exec, graph, 0));
     w->graph = graph;
-    (void)st;
     return BF_OK;
 }
 
@@ -446,7 +454,7 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     if (count && !w->stamp) BF_CUDA(cudaMalloc((void**)&w->stamp, sizeof(int) * C));
     // set-up: lines 1-10 of Algorithm 1
     k_init_counters<<<1, 1, 0, st>>>(w->ctr, cap);
-    BF_CUDA(cudaMemsetAsync(w->fbits, 0, 4 * w->nseg_total, st));
+    BF_CUDA(cudaMemsetAsync(w->fbits, 0, 4 * w->nwords, st));
     k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dG, (const unsigned char*)dAv,
                                                      w->Gint, w->ctr);
     k_init_values<<<blocks_for(C, 256), 256, 0, st>>>(C, (const double*)dT, (const unsigned char*)dTgt,
@@ -454,19 +462,20 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
                                                       w->chg, count ? w->stamp : nullptr, w->ctr);
     InstView v = make_view(a, w);
     if (count) v.stamp = w->stamp;
-    launch_init_propagate(a, w, v, st);
+    k_init_tables<<<blocks_for(C, 256), 256, 0, st>>>(v);
+    launch_setup_frontier(a, w, v, st);
     BF_CUDA(cudaGetLastError());
     double relax_ms = 0.0, prop_ms = 0.0;
-    long long relax_launches = 0;
     if (host_loop) {
         PassTimers tm{};
         if (timed)
             for (int i = 0; i < 4; ++i) BF_CUDA(cudaEventCreate(&tm.e[i]));
         Counters hc;
+        long long launched = 0;
         for (;;) {
             BF_CUDA(cudaMemcpyAsync(&hc, w->ctr, sizeof hc, cudaMemcpyDeviceToHost, st));
             BF_CUDA(cudaStreamSynchronize(st));
-            if (timed && relax_launches > 0) {
+            if (timed && launched > 0) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, tm.e[0], tm.e[1]);
                 relax_ms += ms;
@@ -475,13 +484,13 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
             }
             if (hc.done) break;
             launch_pass_any(a, w, v, st, 0, 0, count, timed ? &tm : nullptr);
-            ++relax_launches;
+            ++launched;
             BF_CUDA(cudaGetLastError());
         }
         if (timed)
             for (int i = 0; i < 4; ++i) cudaEventDestroy(tm.e[i]);
     } else {
-        if ((rc = ws_graph(a, w, st))) return rc;
+        if ((rc = ws_graph(a, w))) return rc;
         BF_CUDA(cudaGraphLaunch(w->exec, st));
     }
     // outputs
@@ -508,9 +517,9 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     *status = hc.status;
     if (opts && opts->stats) {
         bf_solve_stats* o = opts->stats;
-        // set-up: counters, costs, values, first propagate; loop condition
-        // (graph); one relax + propagate per pass; output
-        o->kernel_launches = (host_loop ? 5 : 6) + 2 * hc.round;
+        // set-up: counters, costs, values, tables, first propagate, first
+        // compaction, loop condition (graph); three kernels per pass; output
+        o->kernel_launches = (host_loop ? 7 : 8) + 3 * hc.round;
         o->relaxed_cells = hc.total_relaxed;
         o->executed_pairs = hc.total_relaxed * U;
         o->exact_f1_cells = count ? hc.total_exact : -1;

@@ -99,6 +99,16 @@ def test_random_abstractions(n, periodic, U):
     assert res["iters"] >= 1
 
 
+@pytest.mark.parametrize("n,periodic,reach", [([400], [False], 150), ([400, 6], [False, True], 150)])
+def test_far_boxes_use_the_wide_records(n, periodic, reach):
+    """Boxes whose offset from the cell exceeds the 8-bit relative records are
+    kept as 16-bit absolute records; results are still those of the oracle."""
+    rng = np.random.default_rng(len(n) * 1000 + reach)
+    boxes, G, target, avoid = random_instance(rng, n, periodic, 3, reach=reach)
+    res, ref = check_parity(n, periodic, boxes, G, target=target, avoid=avoid)
+    assert res["iters"] >= 1
+
+
 def test_exact_frontier_count_matches_oracle():
     """Counting mode reproduces |F1| of Algorithm 1 with the exact pred."""
     rng = np.random.default_rng(21)
