@@ -40,6 +40,10 @@ struct bf_solve_ws {
     double* Gint = nullptr;
     Counters* ctr = nullptr;
     int* stamp = nullptr;           // counting mode only
+    long long* cand_key = nullptr;  // input slices of small frontiers
+    int* cand_u = nullptr;
+    int* slice_cnt = nullptr;
+    long long slice_cap = 0;
     // staging for host inputs / outputs
     double* stage_G = nullptr;      // [C][U]
     double* stage_T = nullptr;      // [C]
@@ -63,6 +67,7 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->fbits); cudaFree(w->cells); cudaFree(w->chg); cudaFree(w->Gint); cudaFree(w->ctr);
     cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt); cudaFree(w->stage_avoid);
     cudaFree(w->stage_V); cudaFree(w->trace); cudaFree(w->stamp);
+    cudaFree(w->cand_key); cudaFree(w->cand_u); cudaFree(w->slice_cnt);
     delete w;
 }
 
@@ -157,10 +162,28 @@ __global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_relax(Ins
     const int nchunks = (ncur + 31) >> 5;
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
+    const int U = v.g.U;
     long long relaxed = 0;
     int exact = 0;
-    for (int ch = blockIdx.x * wpb + (threadIdx.x >> 5); ch < nchunks; ch += nwarps)
-        relaxed += relax_chunk<D, FMT, COUNT>(v, ch << 5, ncur - (ch << 5), round, &exact);
+    // small frontier: split each chunk's inputs over S warps
+    int S = 1, q = U;
+    if (v.cand_key && nchunks > 0 && nchunks < kSliceTarget * nwarps) {
+        S = min(U, (kSliceTarget * nwarps + nchunks - 1) / nchunks);
+        q = (U + S - 1) / S;
+        S = (U + q - 1) / q;
+        if ((long long)nchunks * S * 32 > v.slice_cap) { S = 1; q = U; }
+    }
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    if (S == 1) {
+        for (int ch = gw; ch < nchunks; ch += nwarps)
+            relaxed += relax_chunk<D, FMT, COUNT>(v, ch << 5, ncur - (ch << 5), round, &exact);
+    } else {
+        const int items = nchunks * S;
+        for (int it = gw; it < items; it += nwarps) {
+            const int ch = it / S;
+            relaxed += relax_slice<D, FMT, COUNT>(v, ncur, ch, it - ch * S, S, q, round, &exact);
+        }
+    }
     if ((threadIdx.x & 31) == 0) {
         if (relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
         if (COUNT && exact) atomicAdd((unsigned long long*)&k->exact, (unsigned long long)exact);
@@ -283,6 +306,10 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.ctr = w->ctr;
     v.trace = w->trace;
     v.trace_cap = w->trace_cap;
+    v.cand_key = w->cand_key;
+    v.cand_u = w->cand_u;
+    v.slice_cnt = w->slice_cnt;
+    v.slice_cap = w->slice_cap;
     return v;
 }
 
@@ -426,6 +453,21 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
             case 3: set_blocks<3>(a, w); break;
             default: set_blocks<4>(a, w); break;
         }
+        // slice buffers: a sliced pass has nchunks < kSliceTarget x warps and
+        // fewer than 2 x kSliceTarget x warps (chunk, slice) items
+        const long long warps = (long long)w->relax_blocks * 8;
+        const long long cap = 2LL * kSliceTarget * warps * 32;
+        cudaError_t e = cudaMalloc((void**)&w->cand_key, sizeof(long long) * cap);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&w->cand_u, sizeof(int) * cap);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&w->slice_cnt, sizeof(int) * (cap / 32));
+        if (e == cudaSuccess) e = cudaMemsetAsync(w->slice_cnt, 0, sizeof(int) * (cap / 32), st);
+        if (e != cudaSuccess) {
+            cudaFree(w->cand_key); cudaFree(w->cand_u); cudaFree(w->slice_cnt);
+            w->cand_key = nullptr; w->cand_u = nullptr; w->slice_cnt = nullptr;
+            w->relax_blocks = 0;
+            return bfh::cuda_fail(e, "slice buffers");
+        }
+        w->slice_cap = cap;
     }
     // trace buffer (device side), sized to the request
     const long long tcap = (opts && opts->trace) ? opts->trace_cap : 0;

@@ -80,7 +80,17 @@ struct InstView {
     long long* trace;           // [trace_cap][4] or NULL
     long long trace_cap;
     int* stamp;                 // [C] pass that last changed the cell (counting mode) or NULL
+    // input slices (small frontiers): per (chunk, slice) lane candidates and
+    // per chunk arrival counters; NULL -> one warp per chunk over all inputs
+    long long* cand_key;        // [slice_cap]
+    int* cand_u;                // [slice_cap] input (0xFFFF: none) | exact flag << 16
+    int* slice_cnt;             // [slice_cap / 32], zero between passes
+    long long slice_cap;
 };
+
+// Slices: a pass whose frontier has fewer than kSliceTarget x (warps of the
+// relax grid) chunks splits the inputs of each chunk over several warps.
+constexpr int kSliceTarget = 2;
 
 // Host: the abstraction part of a view (grid, dynamics, boxes, pred).
 inline void view_from_abs(InstView& v, const bf_abstraction* a) {
@@ -146,43 +156,97 @@ __device__ __forceinline__ Box<D> decode_compact(unsigned long long r, const Gri
 // gathers
 // ---------------------------------------------------------------------------
 
-// Max of V over the box with the window tables, for a warp whose valid lanes
-// share the box shape: lower corner at c + base, widths w0..w3.  The lookups
-// (row x piece) are enumerated with warp-uniform counters, 8 per round so
-// that 8 loads are in flight.
-template <int D>
-__device__ __forceinline__ long long box_max_rows(const InstView& v, long long c, bool valid, int base, int w0,
-                                                  int w1, int w2, int w3) {
-    const GridDesc& g = v.g;
-    const long long* tab = w0 == 1 ? v.Vkey : (w0 == 2 ? v.M2 : v.M3);
-    const int np = w0 < 3 ? 1 : (w0 + 2) / 3;            // lookups per row
-    const int total = np * w1 * w2 * w3;
-    const int s1 = (int)g.stride[1], s2 = (int)g.stride[2], s3 = (int)g.stride[3];
-    const long long* p = tab + (valid ? c + base : 0);
-    long long m[8];
+// Coordinates of a cell (grids have fewer than 2^31 cells).
+__device__ __forceinline__ void cell_coords32(const GridDesc& g, long long c, int* k) {
+    unsigned r = (unsigned)c;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) m[k] = kKeyMin;
-    int jp = 0, j1 = 0, j2 = 0, j3 = 0;
-    for (int e = 0; e < total; e += 8) {
-        int off[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            off[k] = (w0 < 3 ? 0 : min(3 * jp, w0 - 3)) + j1 * s1 + j2 * s2 + j3 * s3;
-            if (++jp == np) {
-                jp = 0;
-                if (++j1 == w1) {
-                    j1 = 0;
-                    if (++j2 == w2) { j2 = 0; ++j3; }
-                }
-            }
-        }
-        if (valid) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (e + k < total) m[k] = max(m[k], __ldg(p + off[k]));
+    for (int d = 0; d < 4; ++d) {
+        k[d] = 0;
+        if (d < g.D) {
+            k[d] = (int)(r % (unsigned)g.n[d]);
+            r /= (unsigned)g.n[d];
         }
     }
-    return max(max(max(m[0], m[1]), max(m[2], m[3])), max(max(m[4], m[5]), max(m[6], m[7])));
+}
+
+// Max of V over the box of relative record r for the lanes with `mine` set.
+// Those lanes share r and, when r wraps a periodic dim, the coordinates of
+// their cells on the periodic dims, so every lookup (row x piece) lies at the
+// same offset from each lane's cell; lc is one of their cells.  Rows along
+// dim 0 are read from the window tables (V, M2, M3: one lookup covers up to 3
+// cells), so a box takes ceil(w0/3) x w1 x w2 x w3 lookups.  Lane e computes
+// the offset of lookup e once and the warp walks the offsets broadcast by
+// shuffle, four loads in flight.  Must be called by all 32 lanes.
+template <int D>
+__device__ __forceinline__ long long box_max_rows(const InstView& v, long long c, bool mine,
+                                                  unsigned long long r, long long lc) {
+    const GridDesc& g = v.g;
+    const int lane = threadIdx.x & 31;
+    int w[4] = {1, 1, 1, 1}, rel[4] = {0, 0, 0, 0}, k[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        w[d] = rec_byte(r, 2 * d + 1) & 0x7F;
+        rel[d] = rec_sbyte(r, 2 * d);
+    }
+    const bool wrap = (rec_byte(r, 1) & 0x80) != 0;
+    if (wrap) {
+        cell_coords32(g, lc, k);
+#pragma unroll
+        for (int d = 1; d < D; ++d) {
+            int l = k[d] + rel[d];
+            if (g.periodic[d]) {
+                if (l < 0) l += g.n[d];
+                else if (l >= g.n[d]) l -= g.n[d];
+            }
+            lo[d] = l;
+        }
+    }
+    const long long* tab = w[0] == 1 ? v.Vkey : (w[0] == 2 ? v.M2 : v.M3);
+    const int np = w[0] < 3 ? 1 : (w[0] + 2) / 3;            // lookups per row
+    const int total = np * w[1] * w[2] * w[3];
+    const long long* p = tab + (mine ? c + rel[0] : 0);
+    long long m0 = kKeyMin, m1 = kKeyMin;
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        int off = 0;
+        const int e = e0 + lane;
+        if (e < total) {
+            int t = e;
+            const int q = t % np;
+            t /= np;
+            int j[4];
+            j[1] = t % w[1];
+            t /= w[1];
+            j[2] = t % w[2];
+            j[3] = t / w[2];
+            off = w[0] < 3 ? 0 : min(3 * q, w[0] - 3);
+#pragma unroll
+            for (int d = 1; d < D; ++d) {
+                int dl = rel[d] + j[d];
+                if (wrap && g.periodic[d]) {
+                    int x = lo[d] + j[d];
+                    if (x >= g.n[d]) x -= g.n[d];
+                    dl = x - k[d];
+                }
+                off += dl * (int)g.stride[d];
+            }
+        }
+        const int n = min(32, total - e0);
+        int kk = 0;
+        for (; kk + 4 <= n; kk += 4) {
+            const int o0 = __shfl_sync(0xFFFFFFFFu, off, kk), o1 = __shfl_sync(0xFFFFFFFFu, off, kk + 1);
+            const int o2 = __shfl_sync(0xFFFFFFFFu, off, kk + 2), o3 = __shfl_sync(0xFFFFFFFFu, off, kk + 3);
+            if (mine) {
+                const long long a0 = __ldg(p + o0), a1 = __ldg(p + o1), a2 = __ldg(p + o2), a3 = __ldg(p + o3);
+                m0 = max(m0, max(a0, a2));
+                m1 = max(m1, max(a1, a3));
+            }
+        }
+        for (; kk < n; ++kk) {
+            const int o = __shfl_sync(0xFFFFFFFFu, off, kk);
+            if (mine) m0 = max(m0, __ldg(p + o));
+        }
+    }
+    return max(m0, m1);
 }
 
 // Does the box hold a cell whose stamp equals `want` (counting mode)?
@@ -211,29 +275,40 @@ __device__ __forceinline__ bool box_has_stamp(const int* __restrict__ stamp, con
 // relax
 // ---------------------------------------------------------------------------
 
-// Per-lane view of the pair (x, u): validity, shape signature, offset of the
-// lower corner from the cell, widths, and the absolute box when needed.
+// Per-lane view of the pair (x, u): validity, the relative record of its box
+// and the absolute box when needed.
 template <int D>
 struct PairShape {
     bool valid;               // the lane holds a cell and the pair is not blocked
-    bool odd;                 // box wraps or is too wide: gather cell by cell
+    bool slow;                // gathered cell by cell: the box has no relative
+                              // record or wraps a periodic dim 0
     bool have_box;            // b holds the absolute box
-    unsigned long long sig;   // equal signatures + equal base <=> same relative box
-    int base;
-    int w[4];
+    unsigned long long sig;   // relative record (compact form)
+    int wkey;                 // wrapping boxes: the cell's place on the periodic dims
     Box<D> b;
 };
 
+// Place of a cell on the periodic dims >= 1 (lanes with equal keys see a
+// wrapping relative box at equal offsets).
+__device__ __forceinline__ int wrap_key(const GridDesc& g, const int* k) {
+    int key = 1;
+#pragma unroll
+    for (int d = 1; d < 4; ++d)
+        if (d < g.D && g.periodic[d]) key += k[d] * (int)g.stride[d];
+    return key;
+}
+
+// k: the cell's coordinates (only read for wrapping boxes and non-compact
+// formats).
 template <int D, int FMT>
-__device__ __forceinline__ void pair_shape(const InstView& v, long long c, int u, bool act, PairShape<D>& s) {
+__device__ __forceinline__ void pair_shape(const InstView& v, long long c, const int* k, int u, bool act,
+                                           PairShape<D>& s) {
     const GridDesc& g = v.g;
     s.valid = false;
-    s.odd = false;
+    s.slow = false;
     s.have_box = false;
     s.sig = 0;
-    s.base = 0;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) s.w[d] = 1;
+    s.wkey = 0;
     if (!act) return;
     if constexpr (FMT == kBoxCompact) {
         const unsigned long long r =
@@ -242,14 +317,13 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, int u
         if ((f0 & 0x7F) == 0) return;                 // blocked
         s.valid = true;
         s.sig = r;
-        s.odd = (f0 & 0x80) != 0;
-        int base = 0;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            s.w[d] = rec_byte(r, 2 * d + 1) & 0x7F;
-            base += rec_sbyte(r, 2 * d) * (int)g.stride[d];
+        if (f0 & 0x80) {
+            s.wkey = wrap_key(g, k);
+            if (g.periodic[0]) {
+                const int l0 = k[0] + rec_sbyte(r, 0);
+                s.slow = l0 < 0 || l0 + (f0 & 0x7F) > g.n[0];
+            }
         }
-        s.base = base;
     } else {
         Box<D> b;
         if constexpr (FMT == kBoxRecompute) b = make_box<D>(v.dd, g, v.inputs, c, u);
@@ -258,64 +332,79 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, int u
         s.valid = true;
         s.have_box = true;
         s.b = b;
-        long long lin = 0;
-        unsigned long long wp = 0;
+        // the relative record of the box, as the builder encodes it
+        unsigned long long rec = 0;
+        bool wrap = false, bad = false;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
+            const int n = g.n[d];
             const int w = b.hi[d] - b.lo[d] + 1;
-            s.w[d] = w;
-            lin += (long long)b.lo[d] * g.stride[d];
-            wp |= (unsigned long long)(w & 0xFFFF) << (16 * d);
-            s.odd |= w > 0xFFFF;
-            s.odd |= g.periodic[d] && (b.lo[d] + w > g.n[d]);
+            int rel = b.lo[d] - k[d];
+            if (g.periodic[d]) {
+                rel %= n;
+                if (rel < 0) rel += n;
+                if (rel >= n - n / 2) rel -= n;
+                const bool wd = (k[d] + rel < 0) || (k[d] + rel + w > n);
+                wrap |= wd;
+                bad |= d == 0 && wd;
+            }
+            bad |= w > 127 || w < 1 || rel < -128 || rel > 127;
+            rec |= (unsigned long long)(unsigned char)(signed char)rel << (16 * d);
+            rec |= (unsigned long long)(w & 0x7F) << (16 * d + 8);
         }
-        s.base = (int)(lin - c);
-        s.sig = wp;
+        if (wrap) {
+            rec |= 0x80ull << 8;
+            s.wkey = wrap_key(g, k);
+        }
+        s.sig = rec;
+        s.slow = bad;
     }
 }
 
-// Relax cells[first + lane] for lane < count (count <= 32).  Returns the
-// number of cells relaxed; in counting mode adds the cells of the exact F1
-// (some box holds a cell changed in the previous pass) to *exact.
+// Relax the inputs u0 <= u < u1 of the lane's cell c: best (the key to beat,
+// on entry W(c)) and bu (-1, or the lowest input reaching best) are updated
+// on strict decrease; in counting mode in_exact is set when a box holds a
+// cell changed in the previous pass.
 template <int D, int FMT, bool COUNT>
-__device__ __forceinline__ int relax_chunk(const InstView& v, int first, int count, long long round, int* exact) {
+__device__ __forceinline__ void relax_inputs(const InstView& v, long long c, bool act, int u0, int u1,
+                                             long long round, long long& best, int& bu, bool& in_exact) {
     const int lane = threadIdx.x & 31;
     const GridDesc& g = v.g;
-    const bool act = lane < count;
-    const long long c = act ? v.cells[first + lane] : 0;
-    long long best = 0;
-    int bu = -1;
-    bool in_exact = false;
-    if (act) best = v.Vkey[c];
+    int k[4] = {0, 0, 0, 0};
+    if (FMT != kBoxCompact || (g.periodic[0] | g.periodic[1] | g.periodic[2] | g.periodic[3])) cell_coords32(g, c, k);
     // the next input's record and cost are loaded while this one is gathered
     PairShape<D> nx;
-    pair_shape<D, FMT>(v, c, 0, act, nx);
-    double ngv = nx.valid ? __ldcs(v.Gint + c) : 0.0;
-    for (int u = 0; u < g.U; ++u) {
+    pair_shape<D, FMT>(v, c, k, u0, act, nx);
+    double ngv = nx.valid ? __ldcs(v.Gint + (long long)u0 * g.C + c) : 0.0;
+    for (int u = u0; u < u1; ++u) {
         PairShape<D> s = nx;
         const double gv = ngv;
-        if (u + 1 < g.U) {
-            pair_shape<D, FMT>(v, c, u + 1, act, nx);
+        if (u + 1 < u1) {
+            pair_shape<D, FMT>(v, c, k, u + 1, act, nx);
             ngv = nx.valid ? __ldcs(v.Gint + (long long)(u + 1) * g.C + c) : 0.0;
         }
         const unsigned vmask = __ballot_sync(0xFFFFFFFFu, s.valid);
         if (!vmask) continue;
-        const int leader = __ffs(vmask) - 1;
-        const unsigned long long lsig = shfl_u64(s.sig, leader);
-        const int lbase = __shfl_sync(0xFFFFFFFFu, s.base, leader);
-        const bool same = !s.valid || (!s.odd && s.sig == lsig && s.base == lbase);
-        long long m;
-        if (__all_sync(0xFFFFFFFFu, same)) {
-            int lw[4];
-#pragma unroll
-            for (int d = 0; d < 4; ++d) lw[d] = __shfl_sync(0xFFFFFFFFu, s.w[d], leader);
-            m = box_max_rows<D>(v, c, s.valid, lbase, lw[0], lw[1], lw[2], lw[3]);
-        } else {
-            if (s.valid && !s.have_box) {
-                s.b = decode_compact<D>(s.sig, g, c);
-                s.have_box = true;
+        long long m = kKeyMin;
+        unsigned todo = __ballot_sync(0xFFFFFFFFu, s.valid && !s.slow);
+        if (vmask & ~todo) {                                  // boxes without a relative record
+            if (s.valid && s.slow) {
+                if (!s.have_box) {
+                    s.b = decode_compact<D>(s.sig, g, c);
+                    s.have_box = true;
+                }
+                m = box_max<D>(v.Vkey, g, s.b);
             }
-            m = s.valid ? box_max<D>(v.Vkey, g, s.b) : kKeyInf;
+        }
+        while (todo) {                                        // one row gather per group of equal boxes
+            const int leader = __ffs(todo) - 1;
+            const unsigned long long lsig = shfl_u64(s.sig, leader);
+            const int lkey = __shfl_sync(0xFFFFFFFFu, s.wkey, leader);
+            const long long lc = __shfl_sync(0xFFFFFFFFu, (int)c, leader);
+            const bool mine = ((todo >> lane) & 1) && s.sig == lsig && s.wkey == lkey;
+            todo &= ~__ballot_sync(0xFFFFFFFFu, mine);
+            const long long mm = box_max_rows<D>(v, c, mine, lsig, lc);
+            if (mine) m = mm;
         }
         if constexpr (COUNT) {
             if (s.valid && !in_exact) {
@@ -330,6 +419,12 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
         const long long dk = key_of(gv + val_of(m));     // the one FP64 add
         if (dk < best) { best = dk; bu = u; }
     }
+}
+
+// Write the result of a relaxed cell: Vnew, mu and the changed list.
+template <bool COUNT>
+__device__ __forceinline__ void commit_cell(const InstView& v, long long c, long long best, int bu, bool in_exact,
+                                            int* exact) {
     const bool changed = bu >= 0;
     if (changed) {
         v.Vnew[c] = best;
@@ -338,6 +433,66 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
     const int slot = warp_append(changed, &v.ctr->nchg);
     if (changed) v.chg[slot] = (int)c;
     if constexpr (COUNT) *exact += __popc(__ballot_sync(0xFFFFFFFFu, in_exact));
+}
+
+// Relax cells[first + lane] for lane < count (count <= 32) over all inputs.
+// Returns the number of cells relaxed; in counting mode adds the cells of the
+// exact F1 (some box holds a cell changed in the previous pass) to *exact.
+template <int D, int FMT, bool COUNT>
+__device__ __forceinline__ int relax_chunk(const InstView& v, int first, int count, long long round, int* exact) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < count;
+    const long long c = act ? v.cells[first + lane] : 0;
+    long long best = act ? v.Vkey[c] : 0;
+    int bu = -1;
+    bool in_exact = false;
+    relax_inputs<D, FMT, COUNT>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
+    commit_cell<COUNT>(v, c, best, bu, in_exact, exact);
+    return count < 32 ? count : 32;
+}
+
+// Relax slice sl (inputs sl*q .. sl*q+q-1) of chunk ch, one of S slices.  Each
+// slice leaves its lanes' candidates in cand_key / cand_u; the warp that
+// completes the chunk (arrival counter) takes, slice by slice, the strictly
+// smaller candidate -- the same lowest input among the smallest values as one
+// warp going through all inputs -- commits the cells and resets the counter.
+// Returns the cells relaxed (counted by the completing warp).
+template <int D, int FMT, bool COUNT>
+__device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, int sl, int S, int q, long long round,
+                                           int* exact) {
+    const int lane = threadIdx.x & 31;
+    const int first = ch << 5;
+    const int count = ncur - first;
+    const bool act = lane < count;
+    const long long c = act ? v.cells[first + lane] : 0;
+    long long best = act ? v.Vkey[c] : 0;
+    int bu = -1;
+    bool in_exact = false;
+    const int u0 = sl * q;
+    const int u1 = min(v.g.U, u0 + q);
+    relax_inputs<D, FMT, COUNT>(v, c, act, u0, u1, round, best, bu, in_exact);
+    const long long base = (long long)ch * S * 32 + lane;
+    v.cand_key[base + (long long)sl * 32] = best;
+    v.cand_u[base + (long long)sl * 32] = (bu < 0 ? 0xFFFF : bu) | (in_exact ? 1 << 16 : 0);
+    __threadfence();
+    __syncwarp();
+    int prev = 0;
+    if (lane == 0) prev = atomicAdd(v.slice_cnt + ch, 1);
+    prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
+    if (prev != S - 1) return 0;
+    __threadfence();
+    long long b = 0;
+    int bb = -1;
+    bool ex = false;
+    for (int t = 0; t < S; ++t) {
+        const int cu = __ldcg(v.cand_u + base + (long long)t * 32);
+        ex |= (cu >> 16) != 0;
+        if ((cu & 0xFFFF) == 0xFFFF) continue;        // no decrease in this slice
+        const long long ck = __ldcg(v.cand_key + base + (long long)t * 32);
+        if (bb < 0 || ck < b) { b = ck; bb = cu & 0xFFFF; }
+    }
+    if (lane == 0) v.slice_cnt[ch] = 0;
+    commit_cell<COUNT>(v, c, act ? b : 0, act ? bb : -1, act && ex, exact);
     return count < 32 ? count : 32;
 }
 
