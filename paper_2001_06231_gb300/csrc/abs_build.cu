@@ -306,6 +306,7 @@ static int check_grid(const bf_grid* grid, GridDesc& g) {
     }
     for (int d = g.D; d < 4; ++d) { g.n[d] = 1; g.stride[d] = C; }
     g.C = C;
+    grid_divisors(g);
     return BF_OK;
 }
 

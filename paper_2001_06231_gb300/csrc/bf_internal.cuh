@@ -48,7 +48,29 @@ struct GridDesc {
     long long stride[4];   // stride[d] = n[0]*...*n[d-1]
     long long C;
     int U;
+    // x / n[d] for 0 <= x < 2^31 without a divide instruction (division by an
+    // invariant integer, Granlund & Montgomery 1994): with l = ceil(log2 n),
+    // m = floor(2^32 (2^l - n) / n) + 1, x / n = (umulhi(m, x) + x) >> l.
+    unsigned dmul[4];
+    int dshr[4];
 };
+
+// Host: the division constants of every dim (n[d] in 1..2^31-1).
+inline void grid_divisors(GridDesc& g) {
+    for (int d = 0; d < 4; ++d) {
+        const unsigned long long n = (unsigned long long)(g.n[d] > 0 ? g.n[d] : 1);
+        int l = 0;
+        while ((1ull << l) < n) ++l;
+        g.dmul[d] = (unsigned)(((1ull << 32) * ((1ull << l) - n)) / n + 1);
+        g.dshr[d] = l;
+    }
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned grid_div(const GridDesc& g, int d, unsigned x) {
+    return (__umulhi(g.dmul[d], x) + x) >> g.dshr[d];
+}
+#endif
 
 // Box of one (cell, input) pair in registers.
 template <int D>
@@ -136,10 +158,16 @@ __device__ __forceinline__ long long box_max(const long long* __restrict__ V, co
     return m;
 }
 
+// Coordinates of cell c (grids hold fewer than 2^31 cells).
 __device__ __forceinline__ void cell_coords(const GridDesc& g, long long c, int* k) {
+    unsigned r = (unsigned)c;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-        if (d < g.D) { k[d] = (int)(c % g.n[d]); c /= g.n[d]; }
+        if (d < g.D) {
+            const unsigned q = grid_div(g, d, r);
+            k[d] = (int)(r - q * (unsigned)g.n[d]);
+            r = q;
+        }
     }
 }
 

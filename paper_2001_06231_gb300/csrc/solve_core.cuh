@@ -156,19 +156,6 @@ __device__ __forceinline__ Box<D> decode_compact(unsigned long long r, const Gri
 // gathers
 // ---------------------------------------------------------------------------
 
-// Coordinates of a cell (grids have fewer than 2^31 cells).
-__device__ __forceinline__ void cell_coords32(const GridDesc& g, long long c, int* k) {
-    unsigned r = (unsigned)c;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        k[d] = 0;
-        if (d < g.D) {
-            k[d] = (int)(r % (unsigned)g.n[d]);
-            r /= (unsigned)g.n[d];
-        }
-    }
-}
-
 // Max of V over the box of relative record r for the lanes with `mine` set.
 // Those lanes share r and, when r wraps a periodic dim, the coordinates of
 // their cells on the periodic dims, so every lookup (row x piece) lies at the
@@ -190,7 +177,7 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
     }
     const bool wrap = (rec_byte(r, 1) & 0x80) != 0;
     if (wrap) {
-        cell_coords32(g, lc, k);
+        cell_coords(g, lc, k);
 #pragma unroll
         for (int d = 1; d < D; ++d) {
             int l = k[d] + rel[d];
@@ -371,7 +358,7 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
     const int lane = threadIdx.x & 31;
     const GridDesc& g = v.g;
     int k[4] = {0, 0, 0, 0};
-    if (FMT != kBoxCompact || (g.periodic[0] | g.periodic[1] | g.periodic[2] | g.periodic[3])) cell_coords32(g, c, k);
+    if (FMT != kBoxCompact || (g.periodic[0] | g.periodic[1] | g.periodic[2] | g.periodic[3])) cell_coords(g, c, k);
     // the next input's record and cost are loaded while this one is gathered
     PairShape<D> nx;
     pair_shape<D, FMT>(v, c, k, u0, act, nx);
@@ -524,21 +511,25 @@ __device__ __forceinline__ void propagate_cell(const InstView& v, int y, bool co
         if (v.stamp) v.stamp[y] = (int)v.ctr->round;
     }
     const short* q = v.pred + (long long)y * (2 * D);
-    if (q[0] > q[D]) return;                      // y has no predecessor (warp-uniform)
+    short ql[D], qh[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) { ql[d] = q[d]; qh[d] = q[D + d]; }
+    if (ql[0] > qh[0]) return;                    // y has no predecessor (warp-uniform)
     int ky[4];
     cell_coords(g, y, ky);
-    int lo[D], len[D];
+    int lo[4] = {0, 0, 0, 0}, len[4] = {1, 1, 1, 1};
     int rows = 1;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         const int n = g.n[d];
-        int len_d = q[D + d] - q[d] + 1;
+        int len_d = qh[d] - ql[d] + 1;
+        int s = ky[d] + ql[d];
         if (g.periodic[d]) {
-            if (len_d >= n) { lo[d] = 0; len_d = n; }
-            else { int s = (ky[d] + q[d]) % n; if (s < 0) s += n; lo[d] = s; }
-        } else {
-            lo[d] = ky[d] + q[d];
+            if (len_d >= n) { s = 0; len_d = n; }
+            else if (s < 0) s += n;
+            else if (s >= n) s -= n;
         }
+        lo[d] = s;
         len[d] = len_d;
         if (d > 0) rows *= len_d;
     }
@@ -547,22 +538,32 @@ __device__ __forceinline__ void propagate_cell(const InstView& v, int y, bool co
     const int e1 = min(e0, n0 - 1);
     const bool wrap = e0 >= n0;                   // periodic dim 0: the part past n0 - 1 wraps
     for (int r = lane; r < rows; r += 32) {
-        int t = r;
-        long long rowbase = 0;
+        int j[4] = {0, 0, 0, 0};
+        unsigned t = (unsigned)r;
+        if (D == 2) {
+            j[1] = (int)t;
+        } else if (D == 3) {
+            j[2] = (int)(t / (unsigned)len[1]);
+            j[1] = (int)(t - (unsigned)j[2] * (unsigned)len[1]);
+        } else if (D == 4) {
+            const unsigned t2 = t / (unsigned)len[1];
+            j[1] = (int)(t - t2 * (unsigned)len[1]);
+            j[3] = (int)(t2 / (unsigned)len[2]);
+            j[2] = (int)(t2 - (unsigned)j[3] * (unsigned)len[2]);
+        }
+        int rowbase = 0;
 #pragma unroll
         for (int d = 1; d < D; ++d) {
-            const int j = t % len[d];
-            t /= len[d];
-            int xd = lo[d] + j;
+            int xd = lo[d] + j[d];
             if (g.periodic[d] && xd >= g.n[d]) xd -= g.n[d];
-            rowbase += (long long)xd * g.stride[d];
+            rowbase += xd * (int)g.stride[d];
         }
         for (int part = 0; part < (wrap ? 2 : 1); ++part) {
-            const long long a = rowbase + (part ? 0 : a0);
-            const long long b = rowbase + (part ? e0 - n0 : e1);
-            for (long long wd = a >> 5; wd <= (b >> 5); ++wd) {
-                const long long lo_b = max(a, wd << 5), hi_b = min(b, (wd << 5) + 31);
-                mark_word(v.fbits, (int)wd, bit_range((int)(lo_b & 31), (int)(hi_b & 31)));
+            const int a = rowbase + (part ? 0 : a0);
+            const int b = rowbase + (part ? e0 - n0 : e1);
+            for (int wd = a >> 5; wd <= (b >> 5); ++wd) {
+                const int lo_b = max(a, wd << 5), hi_b = min(b, (wd << 5) + 31);
+                mark_word(v.fbits, wd, bit_range(lo_b & 31, hi_b & 31));
             }
         }
     }

@@ -73,3 +73,26 @@ def test_bench_whole_job_aggregation_over_gloo_ranks():
         assert p.exitcode == 0
     for rank, v, u, t in res:
         assert u == 3000.0 and t == 0.75 and abs(v - 4000.0) < 1e-9
+
+
+def test_grid_division_by_multiply_high_is_exact():
+    """Cell coordinates divide by the grid extents with a multiply-high and a
+    shift (division by invariant integers, Granlund & Montgomery 1994):
+    l = ceil(log2 n), m = floor(2^32 (2^l - n) / n) + 1, x // n = (mulhi(m, x) + x) >> l
+    for every extent 1..16383 and every cell index below 2^31."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    xs = np.concatenate([np.arange(0, 70000, dtype=np.uint64),
+                         np.array([2**31 - 1, 2**31 - 2, 2**30, 2**31 - 64], dtype=np.uint64),
+                         rng.integers(0, 2**31, 20000, dtype=np.uint64)])
+    for n in range(1, 16384):
+        l = (n - 1).bit_length()
+        m = ((1 << 32) * ((1 << l) - n)) // n + 1
+        assert 0 < m < (1 << 32)
+        q = (((xs * np.uint64(m)) >> np.uint64(32)) + xs) >> np.uint64(l)
+        assert np.array_equal(q, xs // np.uint64(n)), n
+        # near multiples of n, where an off-by-one would show
+        k = np.arange(1, 2**31 // n, max(1, (2**31 // n) // 500), dtype=np.uint64) * np.uint64(n)
+        for x in (k - np.uint64(1), k):
+            q = (((x * np.uint64(m)) >> np.uint64(32)) + x) >> np.uint64(l)
+            assert np.array_equal(q, x // np.uint64(n)), n
