@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256, 4) k_b_propagate_init(InstView v) {
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
-        propagate_cell<D>(v, v.chg[i], false);
+        propagate_entry<D>(v, i, nchg, false);
 }
 
 // Set-up tail of one instance: compact F1 and decide whether it loops.  The
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256, 4) k_b_propagate(BatchDev b, int g) {
         const int pos = base + item;
         const int i = find_instance(b.scan_chg, beg, end, pos);
         const InstView& v = b.views[i];
-        propagate_cell<D>(v, v.chg[pos - b.scan_chg[i]], true);
+        propagate_entry<D>(v, pos - b.scan_chg[i], v.ctr->nchg, true);
     }
 }
 

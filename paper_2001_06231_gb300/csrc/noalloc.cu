@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256, 4) k_na_propagate(InstView v, int commit)
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
-        propagate_cell<D>(v, v.chg[i], commit != 0);
+        propagate_entry<D>(v, i, nchg, commit != 0);
 }
 
 __global__ void __launch_bounds__(256) k_na_compact(InstView v, long long nwords, int init) {

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_relax(Ins
     }
 }
 
-// Propagate (warp per changed cell): commit W and set F2's bits.
+// Propagate (warp per 32 changed cells): commit W and set F2's bits.
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_propagate(InstView v, int commit) {
     Counters* k = v.ctr;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256, 4) k_propagate(InstView v, int commit) {
     const int wpb = blockDim.x >> 5;
     const int nwarps = gridDim.x * wpb;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nchg; i += nwarps)
-        propagate_cell<D>(v, v.chg[i], commit != 0);
+        propagate_entry<D>(v, i, nchg, commit != 0);
 }
 
 // Compact F2 into the next frontier list, refresh the window tables around

@@ -17,9 +17,10 @@
 //              lowest u among the smallest d; if d < W(x): Vnew(x), mu(x) and
 //              append x to chg.  V and the tables are read-only here, so the
 //              pass is synchronous (Jacobi).
-//   propagate  warp per changed cell y: commit W(y) = Vnew(y), set the bits of
-//              y's predecessor box in fbits (F2 = union of pred of the
-//              changed cells).
+//   propagate  warp per changed cell y: commit W(y) = Vnew(y); a cell that
+//              starts a run of changed cells along a dim-0 row sets the bits
+//              of the run's predecessor boxes in fbits (F2 = union of pred of
+//              the changed cells).
 //   compact    block per 256 bitmap words: F2's bits -> the cell list of the
 //              next pass (ordered within a block; bits cleared on the way);
 //              threads also refresh the window maxima around every changed
@@ -500,46 +501,77 @@ __device__ __forceinline__ unsigned bit_range(int s, int e) {
     return (e == 31 ? 0xFFFFFFFFu : ((1u << (e + 1)) - 1u)) & ~((1u << s) - 1u);
 }
 
-// Commit one changed cell y and set the bits of its predecessor box (a whole
-// warp; lanes take the box's rows, i.e. its dim-0 runs).
+// Changed cells that follow each other along a dim-0 row, in consecutive
+// places of the changed list, form a run.  propagate_entry(i) commits
+// chg[i]; when chg[i] starts a run, it also sets the bits of the bounding box
+// of the run's predecessor boxes in fbits -- their union, for dynamics
+// invariant under translation; a superset otherwise, which relaxes a few
+// extra cells and changes no result, since a cell none of whose boxes holds a
+// changed cell cannot decrease.  Lanes take the rows (dim-0 runs) of the box.
+// Called by a whole warp.
 template <int D>
-__device__ __forceinline__ void propagate_cell(const InstView& v, int y, bool commit) {
+__device__ __forceinline__ void propagate_entry(const InstView& v, int i, int nchg, bool commit) {
     const int lane = threadIdx.x & 31;
     const GridDesc& g = v.g;
+    const int n0 = g.n[0];
+    const int y0 = v.chg[i];
     if (commit && lane == 0) {
-        v.Vkey[y] = v.Vnew[y];
-        if (v.stamp) v.stamp[y] = (int)v.ctr->round;
+        v.Vkey[y0] = v.Vnew[y0];
+        if (v.stamp) v.stamp[y0] = (int)v.ctr->round;
     }
-    const short* q = v.pred + (long long)y * (2 * D);
-    short ql[D], qh[D];
+    const int k0 = y0 - (int)grid_div(g, 0, (unsigned)y0) * n0;
+    if (i > 0 && k0 != 0 && v.chg[i - 1] == y0 - 1) return;     // inside a run
+    // gather the run 32 places at a time; per lane min / max of the box ends
+    int mn[D], mx[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) { ql[d] = q[d]; qh[d] = q[D + d]; }
-    if (ql[0] > qh[0]) return;                    // y has no predecessor (warp-uniform)
-    int ky[4];
-    cell_coords(g, y, ky);
+    for (int d = 0; d < D; ++d) { mn[d] = 0x7FFFFFFF; mx[d] = (int)0x80000000; }
+    int kh[4];
+    cell_coords(g, y0, kh);
+    for (int off = 0;; off += 32) {
+        const int idx = i + off + lane;
+        const int y = idx < nchg ? v.chg[idx] : -1;
+        // lane l is in the run when chg[i + off + l] == y0 + off + l on y0's row
+        const bool in = y >= 0 && y == y0 + off + lane && k0 + off + lane < n0;
+        const unsigned inm = __ballot_sync(0xFFFFFFFFu, in);
+        const unsigned runm = ~inm ? (inm & ((1u << (__ffs(~inm) - 1)) - 1u)) : inm;   // prefix of lanes in the run
+        if ((runm >> lane) & 1) {
+            const short* q = v.pred + (long long)y * (2 * D);
+            const int ql0 = q[0], qh0 = q[D];
+            if (ql0 <= qh0) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const int base = d == 0 ? off + lane : 0;
+                    mn[d] = min(mn[d], base + (int)q[d]);
+                    mx[d] = max(mx[d], base + (int)q[D + d]);
+                }
+            }
+        }
+        if (runm != 0xFFFFFFFFu) break;
+    }
     int lo[4] = {0, 0, 0, 0}, len[4] = {1, 1, 1, 1};
     int rows = 1;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         const int n = g.n[d];
-        int len_d = qh[d] - ql[d] + 1;
-        int s = ky[d] + ql[d];
+        const int a = __reduce_min_sync(0xFFFFFFFFu, mn[d]);
+        const int b = __reduce_max_sync(0xFFFFFFFFu, mx[d]);
+        if (a > b) return;                                        // no predecessor in the run
+        int s = kh[d] + a;
+        int len_d = b - a + 1;
         if (g.periodic[d]) {
             if (len_d >= n) { s = 0; len_d = n; }
-            else if (s < 0) s += n;
-            else if (s >= n) s -= n;
+            else { s %= n; if (s < 0) s += n; }
         }
         lo[d] = s;
         len[d] = len_d;
         if (d > 0) rows *= len_d;
     }
-    const int n0 = g.n[0];
     const int a0 = lo[0], e0 = lo[0] + len[0] - 1;
     const int e1 = min(e0, n0 - 1);
-    const bool wrap = e0 >= n0;                   // periodic dim 0: the part past n0 - 1 wraps
+    const bool wrap = e0 >= n0;                                   // periodic dim 0: the part past n0 - 1 wraps
     for (int r = lane; r < rows; r += 32) {
         int j[4] = {0, 0, 0, 0};
-        unsigned t = (unsigned)r;
+        const unsigned t = (unsigned)r;
         if (D == 2) {
             j[1] = (int)t;
         } else if (D == 3) {
