@@ -311,7 +311,7 @@ def ours(args, rank, world, local_rank):
         "config": {"workload": desc, "cells": C, "inputs": U, "passes": passes,
                    "canonical_relaxations_per_step": canonical, "executed_relaxations_per_step": executed,
                    "l2": "inputs larger than L2 (boxes %d MB + G %d MB > 129 MB)" % (
-                       C * U * 4 * w.grid.ndim >> 20, w.G.nbytes >> 20),
+                       C * U * A.box_record_bytes >> 20, w.G.nbytes >> 20),
                    "abs_build_ms": build_s * 1e3, "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_relax",

@@ -178,8 +178,9 @@ BF_API void abs_free(bf_abstraction *abs);
 /* Statistics of one bf_solve call (all optional outputs). */
 typedef struct {
     int64_t kernel_launches;   /* kernels of this library the call launched      */
-    int64_t relaxed_cells;     /* sum over passes of cells relaxed (frontier as
-                                  flagged through the predecessor boxes)         */
+    int64_t relaxed_cells;     /* sum over passes of cells relaxed (the frontier
+                                  flagged through predecessor bounding boxes:
+                                  a superset of the exact F1)                    */
     int64_t executed_pairs;    /* relaxed_cells * U                              */
     int64_t exact_f1_cells;    /* sum over passes of |F1| with exact pred (only
                                   with BF_FLAG_COUNT_EXACT, else -1)             */
@@ -196,8 +197,9 @@ typedef struct {
     const double *terminal;    /* optional [C] terminal cost (host or device);
                                   NULL -> 0 on target cells, +inf elsewhere     */
     int64_t *trace;            /* optional host [trace_cap][4]: per pass cells
-                                  relaxed, cells changed, active segments, and
-                                  exact |F1| (BF_FLAG_COUNT_EXACT, else -1)      */
+                                  relaxed, cells changed, relax chunks (32
+                                  frontier cells each), and exact |F1|
+                                  (BF_FLAG_COUNT_EXACT, else -1)                  */
     int64_t trace_cap;
     bf_solve_stats *stats;     /* optional output                               */
 } bf_solve_opts;
