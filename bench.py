@@ -169,6 +169,20 @@ def oracle_sample(w, boxes, budget_s=15.0, passes=None):
     return pairs / dt, desc, t_pred, (lambda: run(passes)), passes
 
 
+def host_cpu():
+    """Model name and logical core count of the host (for the CPU baseline)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "%s, %d logical cores on the host" % (model or "unknown CPU", os.cpu_count() or 0)
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -177,7 +191,9 @@ def reference_arm(args, rank, world):
     w, desc = make_workload(args.workload)
     boxes = oracle.build_boxes(w.kind, w.params, w.substeps, w.grid.n, w.grid.lo, w.grid.hi,
                                w.grid.periodic, w.inputs, w.tau)
-    _, sample, _, fn, passes = oracle_sample(w, boxes, budget_s=6.0)
+    # each step re-runs the same bounded sample; about 150 s of CPU time in all
+    _, sample, _, fn, passes = oracle_sample(w, boxes, budget_s=min(6.0, max(0.6, 150.0 / (args.steps + args.warmup + 1))))
+    sample += "; " + host_cpu()
     for _ in range(args.warmup):
         fn()
     tot_pairs, tot_t = 0, 0.0
@@ -213,9 +229,11 @@ def ours(args, rank, world, local_rank):
     C, U = w.ncells, w.ninputs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    A = bf.abs_build_workload(w)
+    A = bf.abs_build_workload(w, mode=bf.MODE_RECOMPUTE if args.recompute else bf.MODE_STORED)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    if args.recompute:
+        desc = desc.replace("stored boxes", "recompute mode") if "stored boxes" in desc else desc + ", recompute mode"
 
     G = torch.from_numpy(w.G).to(dev)
     tg = torch.from_numpy(w.target).to(dev)
@@ -289,7 +307,7 @@ def ours(args, rank, world, local_rank):
     bytes_per_launch = executed * bpp / max(1, passes)
     achieved = bytes_per_launch / (relax_ms_avg / 1e3) / 1e9
     traffic = None
-    if os.path.exists(PROFILE) and args.workload == "unicycle3d":
+    if os.path.exists(PROFILE) and args.workload == "unicycle3d" and not args.recompute:
         kv = dict(l.split(":", 1) for l in open(PROFILE) if ":" in l and not l.startswith("#"))
         if kv.get("kernel_hash", "").strip() == kernel_hash():
             try:
@@ -302,7 +320,7 @@ def ours(args, rank, world, local_rank):
         import oracle
         boxes = A.export_boxes()
         val, sample, _, _, _ = oracle_sample(w, boxes, budget_s=args.cpu_budget)
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + "; " + host_cpu()}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -506,7 +524,10 @@ def served(args):
     for i in range(min(6, len(res_s))):
         k, w, _ = payloads[i % len(payloads)]
         ref = bf.bf_solve(resident[k], w.G, target=w.target, avoid=w.avoid)
-        assert ref["iters"] == res_s[i]["iters"] and ref["status"] == res_s[i]["status"]
+        if res_s[i]["error"]:
+            raise SystemExit("served request %d failed with error %d (budget %.2f GB too small for its system?)"
+                             % (i, res_s[i]["error"], args.budget_gb))
+        assert ref["iters"] == res_s[i]["iters"] and ref["status"] == res_s[i]["status"], i
     qps_p, lat_p = run_plain(arrivals)
     sat = np.zeros(args.requests)
     qps_s_sat, lat_s_sat, _, _ = run_served(sat)
@@ -517,7 +538,7 @@ def served(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "served: Poisson %.0f req/s, %d requests cycling %d payloads over di2d 64x64, "
                                    "unicycle3d 100x100x32, fire4d 60x60x24x6 (tau 2 s); server-resident "
-                                   "abstractions, budget %.0f GB, %d slots, %d passes per engine step" % (
+                                   "abstractions, budget %.2f GB, %d slots, %d passes per engine step" % (
                                        args.rate, args.requests, args.payloads, args.budget_gb, args.max_active,
                                        args.passes),
                        "abstraction_modes": modes},
@@ -545,6 +566,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=64, help="served: requests on the device at once")
     ap.add_argument("--passes", type=int, default=8, help="served: passes per engine step")
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched workload")
+    ap.add_argument("--recompute", action="store_true",
+                    help="build the abstraction in recompute mode (boxes regenerated inside relax)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--host-loop", action="store_true",

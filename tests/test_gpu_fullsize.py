@@ -1,0 +1,87 @@
+"""GPU parity at the measured sizes, in the launch configuration the benchmark
+times (one graph launch per solve, device-resident inputs).
+
+* Unicycle 200 x 200 x 64 x 10 inputs: the oracle solves the exported boxes to
+  the fixed point; V, mu, the pass count, the status and the per-pass changed
+  counts are compared bit for bit, and the Bellman checker runs on every cell.
+* Fire model 100 x 100 x 36 x 8 x 15 inputs (tau 2 s): the whole solve is too
+  slow for the oracle inside a test, so the oracle replays the first passes
+  (cap K, both sides stop with the same state) and the Bellman checker runs on
+  the GPU's fixed point for every cell.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2001_06231_gb300 as bf
+from paper_2001_06231_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+INF = math.inf
+FIRE_TARGET = ((50.0, 250.0), (50.0, 150.0), (-math.radians(30), math.radians(30)), (10.0, 15.0))
+
+
+def same(a, b):
+    return np.array_equal(np.asarray(a), np.asarray(b))
+
+
+def gpu_solve(A, w, **kw):
+    dev = torch.device("cuda", 0)
+    G = torch.from_numpy(w.G).to(dev)
+    tg = torch.from_numpy(w.target).to(dev)
+    av = torch.from_numpy(w.avoid).to(dev)
+    V = torch.empty(w.ncells, dtype=torch.float64, device=dev)
+    mu = torch.empty(w.ncells, dtype=torch.uint8, device=dev)
+    r = bf.bf_solve(A, G, target=tg, avoid=av, V=V, mu=mu, **kw)
+    torch.cuda.synchronize()
+    r["V"] = V.cpu().numpy()
+    r["mu"] = mu.cpu().numpy()
+    return r
+
+
+def test_unicycle_full_size_bit_exact():
+    w = wl.unicycle3d(seed=wl.SEED_BASE + 2)
+    A = bf.abs_build_workload(w)
+    res = gpu_solve(A, w, trace_cap=4096)
+    boxes = A.export_boxes()
+    T = w.terminal()
+    ref = oracle.solve(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid)
+    assert res["status"] == ref["status"] == bf.CONVERGED
+    assert res["iters"] == ref["iters"]
+    assert same(res["V"], ref["V"]), np.nonzero(res["V"] != ref["V"])[0][:10]
+    assert same(res["mu"], ref["mu"])
+    k = ref["iters"]
+    assert same(res["trace"][:k, 1], ref["changed"][:k])
+    assert np.all(res["trace"][:k, 0] >= ref["f1"][:k])
+    nbad, first = oracle.bellman_check(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid, res["V"], res["mu"])
+    assert nbad == 0, first
+    # the value is finite on the target (0) and a decent share of the state space
+    assert np.all(res["V"][w.target.astype(bool)] == 0.0)
+    assert np.isfinite(res["V"]).sum() > 0.5 * w.ncells
+
+
+def test_fire_full_size_prefix_and_bellman():
+    w = wl.fire4d(seed=wl.SEED_BASE + 3, tau=2.0, target=FIRE_TARGET)
+    A = bf.abs_build_workload(w)
+    boxes = A.export_boxes()
+    T = w.terminal()
+    K = 6
+    capped = gpu_solve(A, w, max_iters=K, trace_cap=64)
+    ref = oracle.solve(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid, max_iters=K)
+    assert capped["iters"] == ref["iters"] == K
+    assert capped["status"] == ref["status"]
+    assert same(capped["V"], ref["V"]) and same(capped["mu"], ref["mu"])
+    assert same(capped["trace"][:K, 1], ref["changed"][:K])
+    full = gpu_solve(A, w)
+    assert full["status"] == bf.CONVERGED
+    nbad, first = oracle.bellman_check(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid, full["V"], full["mu"])
+    assert nbad == 0, first
+    # the costs are negative over the fire; avoid cells stay +inf; V <= 0 on the
+    # target (terminal cost 0, lowered only by a cheaper way back); most cells get a value
+    assert (w.G < 0).any()
+    assert np.all(np.isinf(full["V"][w.avoid.astype(bool)]))
+    assert np.all(full["V"][w.target.astype(bool)] <= 0.0)
+    assert np.isfinite(full["V"]).sum() > 0.5 * w.ncells
