@@ -187,7 +187,9 @@ typedef struct {
     int64_t changed_cells;     /* sum over passes of cells whose V decreased    */
     int64_t relax_launches;    /* relax kernels launched                         */
     double relax_ms;           /* summed relax kernel time (BF_FLAG_TIME_KERNELS) */
-    double propagate_ms;       /* summed propagate kernel time (same flag)       */
+    double propagate_ms;       /* summed time of the pass kernel after relax
+                                  (commit, compaction; the predecessor marking
+                                  of Alg. 1's F2 line runs inside relax)        */
 } bf_solve_stats;
 
 typedef struct {

@@ -277,6 +277,31 @@ __global__ void k_pred_pack(GridDesc g, const int* __restrict__ plo, const int* 
     }
 }
 
+// Sum over cells of the dim-0 rows of the predecessor box, and the number of
+// cells that have one: sums[0], sums[1].
+template <int D>
+__global__ void k_pred_rows(GridDesc g, const short* __restrict__ pred, unsigned long long* sums) {
+    unsigned long long rows = 0, cells = 0;
+    for (long long y = blockIdx.x * (long long)blockDim.x + threadIdx.x; y < g.C;
+         y += (long long)gridDim.x * blockDim.x) {
+        const short* q = pred + y * (2 * D);
+        if (q[0] > q[D]) continue;
+        unsigned long long r = 1;
+#pragma unroll
+        for (int d = 1; d < D; ++d) r *= (unsigned long long)(q[D + d] - q[d] + 1);
+        rows += r;
+        cells += 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rows += __shfl_down_sync(0xFFFFFFFFu, rows, o);
+        cells += __shfl_down_sync(0xFFFFFFFFu, cells, o);
+    }
+    if ((threadIdx.x & 31) == 0 && cells) {
+        atomicAdd(sums, rows);
+        atomicAdd(sums + 1, cells);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host API
 // ---------------------------------------------------------------------------
@@ -341,6 +366,17 @@ static int build_pred_t(bf_abstraction* a, cudaStream_t st) {
     BF_CUDA(cudaGetLastError());
     BF_CUDA(cudaFreeAsync(plo, st));
     BF_CUDA(cudaFreeAsync(phi, st));
+    // mean predecessor-box rows: how much marking a changed cell costs
+    unsigned long long* sums = nullptr;
+    unsigned long long h[2] = {0, 0};
+    BF_CUDA(cudaMallocAsync((void**)&sums, 2 * sizeof(unsigned long long), st));
+    BF_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), st));
+    k_pred_rows<D><<<grid_blocks(g.C, 256), 256, 0, st>>>(g, a->d_pred, sums);
+    BF_CUDA(cudaGetLastError());
+    BF_CUDA(cudaMemcpyAsync(h, sums, sizeof h, cudaMemcpyDeviceToHost, st));
+    BF_CUDA(cudaFreeAsync(sums, st));
+    BF_CUDA(cudaStreamSynchronize(st));
+    a->pred_rows = h[1] ? (double)h[0] / (double)h[1] : 0.0;
     return BF_OK;
 }
 

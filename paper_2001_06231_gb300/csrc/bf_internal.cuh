@@ -206,6 +206,7 @@ struct bf_abstraction {
     int box_fmt;              // bfk::kBoxWide / kBoxCompact / kBoxRecompute
     // predecessor index [C][2*D] int16 offsets (x = y + off), empty: lo0 > hi0
     short* d_pred;
+    double pred_rows;         // mean dim-0 rows of a predecessor box (cells with one)
     size_t bytes;
     bf_solve_ws* ws;          // cached workspace of bf_solve
 };

@@ -24,6 +24,9 @@
 
 using namespace bfk;
 
+// Mean predecessor-box rows up to which relax marks the next frontier itself.
+constexpr double kFuseMarkRows = 64.0;
+
 struct bf_solve_ws {
     long long C = 0;
     int U = 0, D = 0;
@@ -56,6 +59,7 @@ struct bf_solve_ws {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     int relax_blocks = 0, prop_blocks = 0, compact_blocks = 0;
+    bool fuse_mark = true;          // relax marks F2 (no propagate launch per pass)
     std::mutex mtx;
 };
 
@@ -153,7 +157,7 @@ __global__ void k_init_counters(Counters* ctr, long long cap) {
 // ---------------------------------------------------------------------------
 // pass kernels
 // ---------------------------------------------------------------------------
-template <int D, int FMT, bool COUNT>
+template <int D, int FMT, bool COUNT, bool MARK>
 __global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_relax(InstView v) {
     Counters* k = v.ctr;
     if (k->done) return;
@@ -176,12 +180,12 @@ __global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_relax(Ins
     const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
     if (S == 1) {
         for (int ch = gw; ch < nchunks; ch += nwarps)
-            relaxed += relax_chunk<D, FMT, COUNT>(v, ch << 5, ncur - (ch << 5), round, &exact);
+            relaxed += relax_chunk<D, FMT, COUNT, MARK>(v, ch << 5, ncur - (ch << 5), round, &exact);
     } else {
         const int items = nchunks * S;
         for (int it = gw; it < items; it += nwarps) {
             const int ch = it / S;
-            relaxed += relax_slice<D, FMT, COUNT>(v, ncur, ch, it - ch * S, S, q, round, &exact);
+            relaxed += relax_slice<D, FMT, COUNT, MARK>(v, ncur, ch, it - ch * S, S, q, round, &exact);
         }
     }
     if ((threadIdx.x & 31) == 0) {
@@ -190,7 +194,8 @@ __global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_relax(Ins
     }
 }
 
-// Propagate (warp per 32 changed cells): commit W and set F2's bits.
+// Propagate (warp per changed cell): set F2's bits from the changed list
+// (set-up: the finite cells; the passes mark F2 inside relax).
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_propagate(InstView v, int commit) {
     Counters* k = v.ctr;
@@ -216,9 +221,15 @@ __global__ void __launch_bounds__(256) k_compact(InstView v, long long nwords, i
     for (long long wb = (long long)blockIdx.x * blockDim.x; wb < nwords; wb += (long long)gridDim.x * blockDim.x)
         compact_words(v, (int)wb, (int)nwords);
     if (!init) {
+        // commit W of the changed cells and refresh the window tables around them
         const int nchg = k->nchg;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchg; i += gridDim.x * blockDim.x)
-            refresh_tables(v, v.chg[i]);
+        const int round = (int)k->round;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchg; i += gridDim.x * blockDim.x) {
+            const int y = v.chg[i];
+            v.Vkey[y] = v.Vnew[y];
+            if (v.stamp) v.stamp[y] = round;
+            refresh_tables(v, y);
+        }
     }
     if (last_block_done(&k->blocks_done)) {
         const int cont = init ? start_loop(v) : finish_pass(v);
@@ -313,16 +324,22 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     return v;
 }
 
-// Launch one pass (relax, propagate, compact).  With timing events, the relax
-// and propagate launches are each bracketed.
+// Launch one pass: relax, then (unless relax marks the next frontier itself)
+// propagate, then compact (which commits W and closes the pass).  With timing
+// events, relax and the rest of the pass are bracketed.
 struct PassTimers {
     cudaEvent_t e[4];
 };
 
 template <int D, int FMT>
 static void launch_relax(bf_solve_ws* w, const InstView& v, cudaStream_t st, bool count) {
-    if (count) k_relax<D, FMT, true><<<w->relax_blocks, 256, 0, st>>>(v);
-    else k_relax<D, FMT, false><<<w->relax_blocks, 256, 0, st>>>(v);
+    if (w->fuse_mark) {
+        if (count) k_relax<D, FMT, true, true><<<w->relax_blocks, 256, 0, st>>>(v);
+        else k_relax<D, FMT, false, true><<<w->relax_blocks, 256, 0, st>>>(v);
+    } else {
+        if (count) k_relax<D, FMT, true, false><<<w->relax_blocks, 256, 0, st>>>(v);
+        else k_relax<D, FMT, false, false><<<w->relax_blocks, 256, 0, st>>>(v);
+    }
 }
 
 template <int D>
@@ -335,9 +352,9 @@ static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView&
         default: launch_relax<D, kBoxWide>(w, v, st, count); break;
     }
     if (tm) { cudaEventRecord(tm->e[1], st); cudaEventRecord(tm->e[2], st); }
-    k_propagate<D><<<w->prop_blocks, 256, 0, st>>>(v, 1);
-    if (tm) cudaEventRecord(tm->e[3], st);
+    if (!w->fuse_mark) k_propagate<D><<<w->prop_blocks, 256, 0, st>>>(v, 0);
     k_compact<<<w->compact_blocks, 256, 0, st>>>(v, w->nwords, 0, h, use_graph);
+    if (tm) cudaEventRecord(tm->e[3], st);
 }
 
 static void launch_pass_any(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
@@ -365,11 +382,14 @@ static void launch_setup_frontier(const bf_abstraction* a, bf_solve_ws* w, const
 template <int D>
 static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
     switch (a->box_fmt) {
-        case kBoxCompact: w->relax_blocks = full_wave(k_relax<D, kBoxCompact, false>, 256); break;
-        case kBoxRecompute: w->relax_blocks = full_wave(k_relax<D, kBoxRecompute, false>, 256); break;
-        default: w->relax_blocks = full_wave(k_relax<D, kBoxWide, false>, 256); break;
+        case kBoxCompact: w->relax_blocks = full_wave(k_relax<D, kBoxCompact, false, true>, 256); break;
+        case kBoxRecompute: w->relax_blocks = full_wave(k_relax<D, kBoxRecompute, false, true>, 256); break;
+        default: w->relax_blocks = full_wave(k_relax<D, kBoxWide, false, true>, 256); break;
     }
     w->prop_blocks = full_wave(k_propagate<D>, 256);
+    // marking inside relax pays when predecessor boxes are small: the marks
+    // then cost less than a separate launch per pass
+    w->fuse_mark = a->pred_rows <= kFuseMarkRows;
     w->compact_blocks = blocks_for(w->nwords, 256);
 }
 
@@ -560,8 +580,9 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     if (opts && opts->stats) {
         bf_solve_stats* o = opts->stats;
         // set-up: counters, costs, values, tables, first propagate, first
-        // compaction, loop condition (graph); three kernels per pass; output
-        o->kernel_launches = (host_loop ? 7 : 8) + 3 * hc.round;
+        // compaction, loop condition (graph); two or three kernels per pass;
+        // output
+        o->kernel_launches = (host_loop ? 7 : 8) + (w->fuse_mark ? 2 : 3) * hc.round;
         o->relaxed_cells = hc.total_relaxed;
         o->executed_pairs = hc.total_relaxed * U;
         o->exact_f1_cells = count ? hc.total_exact : -1;

@@ -11,21 +11,24 @@
 //   cells       i32 [C]    current frontier F1 as a compacted cell list
 //   chg         i32 [C]    cells whose W decreased in the current pass
 //
-// One pass of the while-loop is three kernels:
+// One pass of the while-loop (single solve: two kernels; batched engine and
+// scratch solve: three, with propagate on its own):
 //   relax      warp per 32 cells of F1 (lanes = cells): for u = 0..U-1,
 //              d = G(x,u) + max_{y in F(x,u)} V(y) (one FP64 add, max on keys),
 //              lowest u among the smallest d; if d < W(x): Vnew(x), mu(x) and
 //              append x to chg.  V and the tables are read-only here, so the
-//              pass is synchronous (Jacobi).
-//   propagate  warp per changed cell y: commit W(y) = Vnew(y); a cell that
-//              starts a run of changed cells along a dim-0 row sets the bits
-//              of the run's predecessor boxes in fbits (F2 = union of pred of
-//              the changed cells).
+//              pass is synchronous (Jacobi).  The same warp then sets the bits
+//              of its changed cells' predecessor boxes in fbits (F2 = union of
+//              pred of the changed cells), one box per run of cells along a
+//              dim-0 row.
+//   propagate  (three-kernel form) warp per changed cell y: commit W(y) =
+//              Vnew(y) and mark as above from the changed list.
 //   compact    block per 256 bitmap words: F2's bits -> the cell list of the
 //              next pass (ordered within a block; bits cleared on the way);
-//              threads also refresh the window maxima around every changed
-//              cell; the last block closes the pass (trace, i += 1, loop
-//              condition F1 != empty and i < cap).
+//              threads also commit W = Vnew on the changed cells (two-kernel
+//              form) and refresh the window maxima around them; the last block
+//              closes the pass (trace, i += 1, loop condition F1 != empty and
+//              i < cap).
 //
 // Box gather.  For a pair whose box spans w0 cells along dim 0, one row of
 // the box is max over [lo0, lo0 + w0): one table lookup for w0 <= 3 (V, M2 or
@@ -260,6 +263,188 @@ __device__ __forceinline__ bool box_has_stamp(const int* __restrict__ stamp, con
 }
 
 // ---------------------------------------------------------------------------
+// propagate
+// ---------------------------------------------------------------------------
+
+// Set the bits `mask` of word wd of the upcoming frontier; the word is read
+// first and updated with atomicOr only when some of its bits are still clear
+// (the predecessor boxes of neighbouring changed cells overlap, so most marks
+// end at the read).  Bits only go from 0 to 1 during propagate, so a stale
+// read can only cost a redundant atomic.
+__device__ __forceinline__ void mark_word(unsigned* fbits, int wd, unsigned mask) {
+    if ((fbits[wd] & mask) != mask) atomicOr(&fbits[wd], mask);
+}
+
+__device__ __forceinline__ unsigned bit_range(int s, int e) {
+    return (e == 31 ? 0xFFFFFFFFu : ((1u << (e + 1)) - 1u)) & ~((1u << s) - 1u);
+}
+
+// Set the bits of the box lo[d] .. lo[d] + len[d] - 1 (wrapping on periodic
+// dims; rows = product of len[1..D-1]) in fbits; lanes take the rows.
+template <int D>
+__device__ __forceinline__ void mark_box_rows(const InstView& v, const int* lo, const int* len, int rows) {
+    const int lane = threadIdx.x & 31;
+    const GridDesc& g = v.g;
+    const int n0 = g.n[0];
+    const int a0 = lo[0], e0 = lo[0] + len[0] - 1;
+    const int e1 = min(e0, n0 - 1);
+    const bool wrap = e0 >= n0;                                   // periodic dim 0: the part past n0 - 1 wraps
+    for (int r = lane; r < rows; r += 32) {
+        int j[4] = {0, 0, 0, 0};
+        const unsigned t = (unsigned)r;
+        if (D == 2) {
+            j[1] = (int)t;
+        } else if (D == 3) {
+            j[2] = (int)(t / (unsigned)len[1]);
+            j[1] = (int)(t - (unsigned)j[2] * (unsigned)len[1]);
+        } else if (D == 4) {
+            const unsigned t2 = t / (unsigned)len[1];
+            j[1] = (int)(t - t2 * (unsigned)len[1]);
+            j[3] = (int)(t2 / (unsigned)len[2]);
+            j[2] = (int)(t2 - (unsigned)j[3] * (unsigned)len[2]);
+        }
+        int rowbase = 0;
+#pragma unroll
+        for (int d = 1; d < D; ++d) {
+            int xd = lo[d] + j[d];
+            if (g.periodic[d] && xd >= g.n[d]) xd -= g.n[d];
+            rowbase += xd * (int)g.stride[d];
+        }
+        for (int part = 0; part < (wrap ? 2 : 1); ++part) {
+            const int a = rowbase + (part ? 0 : a0);
+            const int b = rowbase + (part ? e0 - n0 : e1);
+            for (int wd = a >> 5; wd <= (b >> 5); ++wd) {
+                const int lo_b = max(a, wd << 5), hi_b = min(b, (wd << 5) + 31);
+                mark_word(v.fbits, wd, bit_range(lo_b & 31, hi_b & 31));
+            }
+        }
+    }
+}
+
+// Changed cells that follow each other along a dim-0 row, in consecutive
+// places of the changed list, form a run.  propagate_entry(i) commits
+// chg[i]; when chg[i] starts a run, it also sets the bits of the bounding box
+// of the run's predecessor boxes in fbits -- their union, for dynamics
+// invariant under translation; a superset otherwise, which relaxes a few
+// extra cells and changes no result, since a cell none of whose boxes holds a
+// changed cell cannot decrease.  Lanes take the rows (dim-0 runs) of the box.
+// Called by a whole warp.
+template <int D>
+__device__ __forceinline__ void propagate_entry(const InstView& v, int i, int nchg, bool commit) {
+    const int lane = threadIdx.x & 31;
+    const GridDesc& g = v.g;
+    const int n0 = g.n[0];
+    const int y0 = v.chg[i];
+    if (commit && lane == 0) {
+        v.Vkey[y0] = v.Vnew[y0];
+        if (v.stamp) v.stamp[y0] = (int)v.ctr->round;
+    }
+    const int k0 = y0 - (int)grid_div(g, 0, (unsigned)y0) * n0;
+    if (i > 0 && k0 != 0 && v.chg[i - 1] == y0 - 1) return;     // inside a run
+    // gather the run 32 places at a time; per lane min / max of the box ends
+    int mn[D], mx[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) { mn[d] = 0x7FFFFFFF; mx[d] = (int)0x80000000; }
+    int kh[4];
+    cell_coords(g, y0, kh);
+    for (int off = 0;; off += 32) {
+        const int idx = i + off + lane;
+        const int y = idx < nchg ? v.chg[idx] : -1;
+        // lane l is in the run when chg[i + off + l] == y0 + off + l on y0's row
+        const bool in = y >= 0 && y == y0 + off + lane && k0 + off + lane < n0;
+        const unsigned inm = __ballot_sync(0xFFFFFFFFu, in);
+        const unsigned runm = ~inm ? (inm & ((1u << (__ffs(~inm) - 1)) - 1u)) : inm;   // prefix of lanes in the run
+        if ((runm >> lane) & 1) {
+            const short* q = v.pred + (long long)y * (2 * D);
+            const int ql0 = q[0], qh0 = q[D];
+            if (ql0 <= qh0) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const int base = d == 0 ? off + lane : 0;
+                    mn[d] = min(mn[d], base + (int)q[d]);
+                    mx[d] = max(mx[d], base + (int)q[D + d]);
+                }
+            }
+        }
+        if (runm != 0xFFFFFFFFu) break;
+    }
+    int lo[4] = {0, 0, 0, 0}, len[4] = {1, 1, 1, 1};
+    int rows = 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int n = g.n[d];
+        const int a = __reduce_min_sync(0xFFFFFFFFu, mn[d]);
+        const int b = __reduce_max_sync(0xFFFFFFFFu, mx[d]);
+        if (a > b) return;                                        // no predecessor in the run
+        int s = kh[d] + a;
+        int len_d = b - a + 1;
+        if (g.periodic[d]) {
+            if (len_d >= n) { s = 0; len_d = n; }
+            else { s %= n; if (s < 0) s += n; }
+        }
+        lo[d] = s;
+        len[d] = len_d;
+        if (d > 0) rows *= len_d;
+    }
+    mark_box_rows<D>(v, lo, len, rows);
+}
+
+// Set the bits of the predecessor boxes of the changed lanes' cells y in
+// fbits (whole warp; relax calls it right after deciding its cells, so the
+// frontier of the next pass is built while the pass runs).  Changed cells
+// that follow each other along a dim-0 row in consecutive lanes form a run,
+// which marks the bounding box of its cells' predecessor boxes (the same
+// superset argument as propagate_entry).
+template <int D>
+__device__ __forceinline__ void mark_changed(const InstView& v, int y, bool changed) {
+    const int lane = threadIdx.x & 31;
+    const GridDesc& g = v.g;
+    int ql[D], qh[D];
+    int ky[4] = {0, 0, 0, 0};
+    bool has = false;
+#pragma unroll
+    for (int d = 0; d < D; ++d) { ql[d] = 0; qh[d] = -1; }
+    if (changed) {
+        const short* q = v.pred + (long long)y * (2 * D);
+#pragma unroll
+        for (int d = 0; d < D; ++d) { ql[d] = q[d]; qh[d] = q[D + d]; }
+        has = ql[0] <= qh[0];                    // else y has no predecessor
+        if (has) cell_coords(g, y, ky);
+    }
+    const int yprev = __shfl_up_sync(0xFFFFFFFFu, y, 1);
+    const int hprev = __shfl_up_sync(0xFFFFFFFFu, has ? 1 : 0, 1);
+    const bool cont = has && lane > 0 && hprev && y == yprev + 1 && ky[0] != 0;
+    const unsigned contm = __ballot_sync(0xFFFFFFFFu, cont);
+    unsigned heads = __ballot_sync(0xFFFFFFFFu, has && !cont);
+    while (heads) {
+        const int h = __ffs(heads) - 1;
+        heads &= heads - 1;
+        const unsigned above = h < 31 ? (contm >> (h + 1)) : 0u;
+        const int last = h + __ffs(~above) - 1;          // the run is lanes h..last
+        const bool in = lane >= h && lane <= last;
+        int lo[4] = {0, 0, 0, 0}, len[4] = {1, 1, 1, 1};
+        int rows = 1;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int n = g.n[d];
+            const int base = d == 0 ? ky[0] : 0;
+            const int mn = __reduce_min_sync(0xFFFFFFFFu, in ? base + ql[d] : 0x7FFFFFFF);
+            const int mx = __reduce_max_sync(0xFFFFFFFFu, in ? base + qh[d] : (int)0x80000000);
+            int s = mn + (d == 0 ? 0 : __shfl_sync(0xFFFFFFFFu, ky[d], h));
+            int len_d = mx - mn + 1;
+            if (g.periodic[d]) {
+                if (len_d >= n) { s = 0; len_d = n; }
+                else { s %= n; if (s < 0) s += n; }
+            }
+            lo[d] = s;
+            len[d] = len_d;
+            if (d > 0) rows *= len_d;
+        }
+        mark_box_rows<D>(v, lo, len, rows);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // relax
 // ---------------------------------------------------------------------------
 
@@ -409,8 +594,9 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
     }
 }
 
-// Write the result of a relaxed cell: Vnew, mu and the changed list.
-template <bool COUNT>
+// Write the result of a relaxed cell: Vnew, mu and the changed list; with
+// MARK also the predecessor boxes of the changed cells into the next frontier.
+template <int D, bool COUNT, bool MARK>
 __device__ __forceinline__ void commit_cell(const InstView& v, long long c, long long best, int bu, bool in_exact,
                                             int* exact) {
     const bool changed = bu >= 0;
@@ -421,12 +607,14 @@ __device__ __forceinline__ void commit_cell(const InstView& v, long long c, long
     const int slot = warp_append(changed, &v.ctr->nchg);
     if (changed) v.chg[slot] = (int)c;
     if constexpr (COUNT) *exact += __popc(__ballot_sync(0xFFFFFFFFu, in_exact));
+    if constexpr (MARK) mark_changed<D>(v, changed ? (int)c : -1, changed);
 }
 
 // Relax cells[first + lane] for lane < count (count <= 32) over all inputs.
 // Returns the number of cells relaxed; in counting mode adds the cells of the
 // exact F1 (some box holds a cell changed in the previous pass) to *exact.
-template <int D, int FMT, bool COUNT>
+// MARK: also set the next frontier's bits (no separate propagate launch).
+template <int D, int FMT, bool COUNT, bool MARK = false>
 __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int count, long long round, int* exact) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < count;
@@ -435,7 +623,7 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
     int bu = -1;
     bool in_exact = false;
     relax_inputs<D, FMT, COUNT>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
-    commit_cell<COUNT>(v, c, best, bu, in_exact, exact);
+    commit_cell<D, COUNT, MARK>(v, c, best, bu, in_exact, exact);
     return count < 32 ? count : 32;
 }
 
@@ -445,7 +633,7 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
 // smaller candidate -- the same lowest input among the smallest values as one
 // warp going through all inputs -- commits the cells and resets the counter.
 // Returns the cells relaxed (counted by the completing warp).
-template <int D, int FMT, bool COUNT>
+template <int D, int FMT, bool COUNT, bool MARK = false>
 __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, int sl, int S, int q, long long round,
                                            int* exact) {
     const int lane = threadIdx.x & 31;
@@ -480,139 +668,23 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
         if (bb < 0 || ck < b) { b = ck; bb = cu & 0xFFFF; }
     }
     if (lane == 0) v.slice_cnt[ch] = 0;
-    commit_cell<COUNT>(v, c, act ? b : 0, act ? bb : -1, act && ex, exact);
+    commit_cell<D, COUNT, MARK>(v, c, act ? b : 0, act ? bb : -1, act && ex, exact);
     return count < 32 ? count : 32;
-}
-
-// ---------------------------------------------------------------------------
-// propagate
-// ---------------------------------------------------------------------------
-
-// Set the bits `mask` of word wd of the upcoming frontier; the word is read
-// first and updated with atomicOr only when some of its bits are still clear
-// (the predecessor boxes of neighbouring changed cells overlap, so most marks
-// end at the read).  Bits only go from 0 to 1 during propagate, so a stale
-// read can only cost a redundant atomic.
-__device__ __forceinline__ void mark_word(unsigned* fbits, int wd, unsigned mask) {
-    if ((fbits[wd] & mask) != mask) atomicOr(&fbits[wd], mask);
-}
-
-__device__ __forceinline__ unsigned bit_range(int s, int e) {
-    return (e == 31 ? 0xFFFFFFFFu : ((1u << (e + 1)) - 1u)) & ~((1u << s) - 1u);
-}
-
-// Changed cells that follow each other along a dim-0 row, in consecutive
-// places of the changed list, form a run.  propagate_entry(i) commits
-// chg[i]; when chg[i] starts a run, it also sets the bits of the bounding box
-// of the run's predecessor boxes in fbits -- their union, for dynamics
-// invariant under translation; a superset otherwise, which relaxes a few
-// extra cells and changes no result, since a cell none of whose boxes holds a
-// changed cell cannot decrease.  Lanes take the rows (dim-0 runs) of the box.
-// Called by a whole warp.
-template <int D>
-__device__ __forceinline__ void propagate_entry(const InstView& v, int i, int nchg, bool commit) {
-    const int lane = threadIdx.x & 31;
-    const GridDesc& g = v.g;
-    const int n0 = g.n[0];
-    const int y0 = v.chg[i];
-    if (commit && lane == 0) {
-        v.Vkey[y0] = v.Vnew[y0];
-        if (v.stamp) v.stamp[y0] = (int)v.ctr->round;
-    }
-    const int k0 = y0 - (int)grid_div(g, 0, (unsigned)y0) * n0;
-    if (i > 0 && k0 != 0 && v.chg[i - 1] == y0 - 1) return;     // inside a run
-    // gather the run 32 places at a time; per lane min / max of the box ends
-    int mn[D], mx[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) { mn[d] = 0x7FFFFFFF; mx[d] = (int)0x80000000; }
-    int kh[4];
-    cell_coords(g, y0, kh);
-    for (int off = 0;; off += 32) {
-        const int idx = i + off + lane;
-        const int y = idx < nchg ? v.chg[idx] : -1;
-        // lane l is in the run when chg[i + off + l] == y0 + off + l on y0's row
-        const bool in = y >= 0 && y == y0 + off + lane && k0 + off + lane < n0;
-        const unsigned inm = __ballot_sync(0xFFFFFFFFu, in);
-        const unsigned runm = ~inm ? (inm & ((1u << (__ffs(~inm) - 1)) - 1u)) : inm;   // prefix of lanes in the run
-        if ((runm >> lane) & 1) {
-            const short* q = v.pred + (long long)y * (2 * D);
-            const int ql0 = q[0], qh0 = q[D];
-            if (ql0 <= qh0) {
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const int base = d == 0 ? off + lane : 0;
-                    mn[d] = min(mn[d], base + (int)q[d]);
-                    mx[d] = max(mx[d], base + (int)q[D + d]);
-                }
-            }
-        }
-        if (runm != 0xFFFFFFFFu) break;
-    }
-    int lo[4] = {0, 0, 0, 0}, len[4] = {1, 1, 1, 1};
-    int rows = 1;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-        const int n = g.n[d];
-        const int a = __reduce_min_sync(0xFFFFFFFFu, mn[d]);
-        const int b = __reduce_max_sync(0xFFFFFFFFu, mx[d]);
-        if (a > b) return;                                        // no predecessor in the run
-        int s = kh[d] + a;
-        int len_d = b - a + 1;
-        if (g.periodic[d]) {
-            if (len_d >= n) { s = 0; len_d = n; }
-            else { s %= n; if (s < 0) s += n; }
-        }
-        lo[d] = s;
-        len[d] = len_d;
-        if (d > 0) rows *= len_d;
-    }
-    const int a0 = lo[0], e0 = lo[0] + len[0] - 1;
-    const int e1 = min(e0, n0 - 1);
-    const bool wrap = e0 >= n0;                                   // periodic dim 0: the part past n0 - 1 wraps
-    for (int r = lane; r < rows; r += 32) {
-        int j[4] = {0, 0, 0, 0};
-        const unsigned t = (unsigned)r;
-        if (D == 2) {
-            j[1] = (int)t;
-        } else if (D == 3) {
-            j[2] = (int)(t / (unsigned)len[1]);
-            j[1] = (int)(t - (unsigned)j[2] * (unsigned)len[1]);
-        } else if (D == 4) {
-            const unsigned t2 = t / (unsigned)len[1];
-            j[1] = (int)(t - t2 * (unsigned)len[1]);
-            j[3] = (int)(t2 / (unsigned)len[2]);
-            j[2] = (int)(t2 - (unsigned)j[3] * (unsigned)len[2]);
-        }
-        int rowbase = 0;
-#pragma unroll
-        for (int d = 1; d < D; ++d) {
-            int xd = lo[d] + j[d];
-            if (g.periodic[d] && xd >= g.n[d]) xd -= g.n[d];
-            rowbase += xd * (int)g.stride[d];
-        }
-        for (int part = 0; part < (wrap ? 2 : 1); ++part) {
-            const int a = rowbase + (part ? 0 : a0);
-            const int b = rowbase + (part ? e0 - n0 : e1);
-            for (int wd = a >> 5; wd <= (b >> 5); ++wd) {
-                const int lo_b = max(a, wd << 5), hi_b = min(b, (wd << 5) + 31);
-                mark_word(v.fbits, wd, bit_range(lo_b & 31, hi_b & 31));
-            }
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
 // window tables
 // ---------------------------------------------------------------------------
 
-// Recompute M2 and M3 at cell e from V (entries past a non-periodic row end
-// take the max over the part inside the row; boxes never read them).
+// Recompute M2 and M3 at cell e from the values at the end of the pass (Vnew,
+// equal to V on every cell not changed in it; entries past a non-periodic
+// row end take the max over the part inside the row; boxes never read them).
 __device__ __forceinline__ void table_entry(const InstView& v, long long e) {
     const GridDesc& g = v.g;
     const int n0 = g.n[0];
-    const long long row = e - (e % n0);
+    const long long row = (long long)grid_div(g, 0, (unsigned)e) * n0;
     const int x = (int)(e - row);
-    const long long m = v.Vkey[e];
+    const long long m = v.Vnew[e];
     long long m2 = m, m3 = m;
     for (int j = 1; j < 3; ++j) {
         int xj = x + j;
@@ -620,7 +692,7 @@ __device__ __forceinline__ void table_entry(const InstView& v, long long e) {
             if (!g.periodic[0]) break;
             xj -= n0;
         }
-        const long long val = v.Vkey[row + xj];
+        const long long val = v.Vnew[row + xj];
         if (j == 1) m2 = max(m2, val);
         m3 = max(m3, val);
     }
@@ -633,7 +705,7 @@ __device__ __forceinline__ void table_entry(const InstView& v, long long e) {
 __device__ __forceinline__ void refresh_tables(const InstView& v, long long y) {
     const GridDesc& g = v.g;
     const int n0 = g.n[0];
-    const long long row = y - (y % n0);
+    const long long row = (long long)grid_div(g, 0, (unsigned)y) * n0;
     const int x = (int)(y - row);
     for (int j = 0; j < 3 && j < n0; ++j) {
         int xe = x - j;
