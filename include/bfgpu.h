@@ -165,9 +165,21 @@ BF_API int abs_info(const bf_abstraction *abs, int64_t *ncells, int32_t *ninputs
  * free it while a solve on it is running. */
 BF_API void abs_free(bf_abstraction *abs);
 
+/* Pass schedules (bf_solve_opts.schedule).
+ * BF_SCHED_JACOBI (default): every relaxation of a pass reads W as it stood at
+ *   the start of the pass; V, mu, the pass count and every per-pass frontier
+ *   are deterministic (and equal to the CPU oracle's).
+ * BF_SCHED_INPLACE: a decrease of W(x) is written at once, so relaxations later
+ *   in the same pass may read it -- the in-place writes of Alg. 1's for-loop,
+ *   whose processing order the paper leaves open (Sec. IV-A).  Every update is
+ *   W <- min(W, G + max W) with a monotone operator, so a run that stops with
+ *   F1 empty reaches the same V (the greatest fixed point below the terminal
+ *   cost), usually in fewer passes; mu is a controller realizing V (Thm. 2's
+ *   construction) but not necessarily the Jacobi one, and the pass count,
+ *   trace and exact-F1 counts depend on the order warps run in. */
+#define BF_SCHED_JACOBI 0
 #define BF_SCHED_AUTO 0
-#define BF_SCHED_SEGMENT 1     /* warp per 32 consecutive cells (lanes = cells) */
-#define BF_SCHED_LIST 2        /* warp per cells in a list (lanes = inputs)     */
+#define BF_SCHED_INPLACE 1
 
 #define BF_FLAG_HOST_LOOP 1    /* drive passes from the host (one sync per pass) */
 #define BF_FLAG_COUNT_EXACT 2  /* also count |F1| of Algorithm 1 with the exact

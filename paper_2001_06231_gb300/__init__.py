@@ -27,7 +27,8 @@ HANDOVER = 0xFF
 BLOCKED = -32768
 LINEAR2D, UNICYCLE3D, FIRE4D = 1, 2, 3
 MODE_STORED, MODE_RECOMPUTE = 0, 1
-SCHED_AUTO, SCHED_SEGMENT, SCHED_LIST = 0, 1, 2
+SCHED_JACOBI, SCHED_INPLACE = 0, 1
+SCHED_AUTO = SCHED_JACOBI
 FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 
 EXPORTED = ["abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",

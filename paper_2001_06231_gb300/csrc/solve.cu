@@ -60,6 +60,7 @@ struct bf_solve_ws {
     cudaGraph_t graph = nullptr;
     int relax_blocks = 0, prop_blocks = 0, compact_blocks = 0;
     bool fuse_mark = true;          // relax marks F2 (no propagate launch per pass)
+    int inplace = 0;                // schedule the views (and the graph) were made for
     std::mutex mtx;
 };
 
@@ -321,6 +322,7 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.cand_u = w->cand_u;
     v.slice_cnt = w->slice_cnt;
     v.slice_cap = w->slice_cap;
+    v.inplace = w->inplace;
     return v;
 }
 
@@ -488,6 +490,17 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
             return bfh::cuda_fail(e, "slice buffers");
         }
         w->slice_cap = cap;
+    }
+    // schedule (the graph holds the view by value: rebuild it on a change)
+    const int sched = opts ? opts->schedule : BF_SCHED_JACOBI;
+    if (sched != BF_SCHED_JACOBI && sched != BF_SCHED_INPLACE) {
+        bfh::set_error("bf_solve: unknown schedule %d", sched);
+        return BF_ERR_INVALID;
+    }
+    if (sched != w->inplace) {
+        if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+        if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
+        w->inplace = sched;
     }
     // trace buffer (device side), sized to the request
     const long long tcap = (opts && opts->trace) ? opts->trace_cap : 0;

@@ -90,6 +90,7 @@ struct InstView {
     int* cand_u;                // [slice_cap] input (0xFFFF: none) | exact flag << 16
     int* slice_cnt;             // [slice_cap / 32], zero between passes
     long long slice_cap;
+    int inplace;                // BF_SCHED_INPLACE: a decrease is written to Vkey at once
 };
 
 // Slices: a pass whose frontier has fewer than kSliceTarget x (warps of the
@@ -602,6 +603,7 @@ __device__ __forceinline__ void commit_cell(const InstView& v, long long c, long
     const bool changed = bu >= 0;
     if (changed) {
         v.Vnew[c] = best;
+        if (v.inplace) v.Vkey[c] = best;         // visible to the rest of this pass
         v.mu[c] = (unsigned char)bu;
     }
     const int slot = warp_append(changed, &v.ctr->nchg);

@@ -202,3 +202,48 @@ def test_builder_and_solver_parity(which):
     assert same(R.export_boxes(), gb)
     rr = bf.bf_solve(R, w.G, target=w.target, avoid=w.avoid)
     assert same(rr["V"], res["V"]) and same(rr["mu"], res["mu"]) and rr["iters"] == res["iters"]
+
+
+def check_inplace(n, periodic, boxes, G, terminal, avoid, A=None):
+    """In-place passes: the oracle's (Jacobi) V bit for bit, no more passes, and
+    a controller that attains V (Bellman check); negative cycles still hit the cap."""
+    D = len(n)
+    if A is None:
+        A = bf.abs_from_boxes(bf.make_grid(n, [0.0] * D, [float(k) for k in n], periodic), boxes)
+    ref = oracle.solve(n, periodic, boxes, G, terminal, avoid)
+    r = bf.bf_solve(A, G, terminal=terminal, avoid=avoid, schedule=bf.SCHED_INPLACE)
+    if ref["status"] != bf.CONVERGED:
+        assert r["status"] == ref["status"]
+        return r, ref
+    assert r["status"] == bf.CONVERGED
+    assert same(r["V"], ref["V"]), np.nonzero(r["V"] != ref["V"])[0][:10]
+    assert r["iters"] <= ref["iters"]
+    nbad, first = oracle.bellman_check(n, periodic, boxes, G, terminal, avoid, r["V"], r["mu"])
+    assert nbad == 0, first
+    return r, ref
+
+
+@pytest.mark.parametrize("n,periodic,U,neg", [
+    ([45, 29], [False, False], 5, False), ([21, 17, 12], [False, False, True], 6, False),
+    ([13, 11, 9, 6], [False, False, True, False], 7, False), ([300], [False], 2, False),
+    ([33, 20], [False, True], 4, True), ([70, 5, 6], [True, False, True], 4, True),
+])
+def test_inplace_schedule_reaches_the_same_value(n, periodic, U, neg):
+    rng = np.random.default_rng(hash((tuple(n), U, neg, "inplace")) % 2**32)
+    boxes, G, target, avoid = random_instance(rng, n, periodic, U, neg=neg)
+    terminal = np.where(target.astype(bool), 0.0, INF)
+    check_inplace(n, periodic, boxes, G, terminal, avoid)
+
+
+@pytest.mark.parametrize("which", ["unicycle", "fire"])
+def test_inplace_schedule_builder_workloads(which):
+    if which == "unicycle":
+        w = wl.unicycle3d(n=(60, 50, 24), n_obstacles=8)
+    else:
+        w = wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0)))
+    A = bf.abs_build_workload(w)
+    r, ref = check_inplace(w.grid.n, w.grid.periodic, A.export_boxes(), w.G, w.terminal(), w.avoid, A=A)
+    # Jacobi again on the same handle: the graph is rebuilt for the schedule
+    j = bf.bf_solve(A, w.G, target=w.target, avoid=w.avoid)
+    assert j["iters"] == ref["iters"] and same(j["V"], ref["V"]) and same(j["mu"], ref["mu"])
+    print("%s: %d in-place passes vs %d Jacobi passes" % (which, r["iters"], ref["iters"]))
