@@ -102,6 +102,8 @@ extern "C" {
  * 4*D*C*U fewer bytes, far more FP64 work). */
 #define BF_MODE_STORED 0
 #define BF_MODE_RECOMPUTE 1
+#define BF_MODE_HYBRID 2       /* records of the first K inputs stored, the
+                                  rest regenerated (abs_build_hybrid)       */
 
 typedef struct {
     int32_t ndim;          /* D, 1..4                                   */
@@ -135,6 +137,24 @@ typedef struct bf_abstraction bf_abstraction;   /* opaque, device-resident */
  * BF_ERR_CUDA. */
 BF_API int abs_build(const bf_dynamics *dyn, const bf_grid *grid, const bf_inputs *inputs,
               double tau, int32_t mode, void *stream, bf_abstraction **out);
+
+/* abs_build_hybrid -- the memory regulation of Sec. IV-B between the two modes
+ * above: store the images of F while memory allows, recompute the rest.  The
+ * box records of the first K inputs are stored, K the most inputs whose
+ * compact records (4 bytes per (cell, input) for D <= 2, 8 for D >= 3) fit
+ * in box_budget bytes; the boxes of the other inputs are regenerated inside
+ * the relaxation kernel.  K = U gives a stored-mode abstraction, K = 0 (or a
+ * system whose boxes do not fit the compact records) a recompute-mode one;
+ * otherwise the mode is BF_MODE_HYBRID.  Boxes, and so every result, are
+ * bit-identical to the other modes.  The predecessor index and the inputs
+ * are not counted in box_budget.  Errors: as abs_build, and BF_ERR_INVALID
+ * for a negative budget. */
+BF_API int abs_build_hybrid(const bf_dynamics *dyn, const bf_grid *grid, const bf_inputs *inputs,
+              double tau, int64_t box_budget, void *stream, bf_abstraction **out);
+
+/* abs_stored_inputs -- K, the inputs whose box records are stored (U in
+ * stored mode, 0 in recompute mode).  Errors: BF_ERR_INVALID on NULL. */
+BF_API int abs_stored_inputs(const bf_abstraction *abs, int32_t *nstored);
 
 /* abs_from_boxes -- abstraction from caller-supplied boxes in the external
  * layout int16 [C][U][2][D] (host or device).  Every box is validated on the
@@ -255,8 +275,10 @@ BF_API int bf_solve_batch(int32_t n, const bf_abstraction *const *abs, const dou
  * caller) or a system (dyn, grid, inputs, tau); the server keeps the
  * abstractions it builds resident and reuses them for later requests with
  * the same system (compared field by field).  A new abstraction is built in
- * STORED mode when its boxes fit the remaining budget, else in RECOMPUTE mode
- * (the memory control of Sec. IV-B). */
+ * STORED mode when its boxes fit the remaining budget, else in HYBRID mode
+ * with the records of as many inputs as the rest of the budget holds (see
+ * abs_build_hybrid), else in RECOMPUTE mode (the memory control of
+ * Sec. IV-B); bf_result.mode reports which. */
 typedef struct bf_server bf_server;
 
 typedef struct {

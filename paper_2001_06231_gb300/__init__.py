@@ -26,12 +26,13 @@ CONVERGED, NEG_CYCLE, ITER_CAP = 0, 1, 2
 HANDOVER = 0xFF
 BLOCKED = -32768
 LINEAR2D, UNICYCLE3D, FIRE4D = 1, 2, 3
-MODE_STORED, MODE_RECOMPUTE = 0, 1
+MODE_STORED, MODE_RECOMPUTE, MODE_HYBRID = 0, 1, 2
 SCHED_JACOBI, SCHED_INPLACE = 0, 1
 SCHED_AUTO = SCHED_JACOBI
 FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 
-EXPORTED = ["abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
+EXPORTED = ["abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes", "abs_export_boxes",
+            "abs_export_pred", "abs_info",
             "abs_free", "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
             "bf_serve_close", "bf_solve_noalloc", "bf_last_error"]
 
@@ -104,6 +105,8 @@ def lib():
             raise BfError(-5, "library %s lacks %s" % (path, ", ".join(missing)))
         P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         L.abs_build.argtypes = [P, P, P, f64, i32, P, P]
+        L.abs_build_hybrid.argtypes = [P, P, P, f64, i64, P, P]
+        L.abs_stored_inputs.argtypes = [P, P]
         L.abs_from_boxes.argtypes = [P, i32, P, P, P]
         L.abs_export_boxes.argtypes = [P, P, P]
         L.abs_export_pred.argtypes = [P, P, P]
@@ -119,7 +122,8 @@ def lib():
         L.bf_serve_close.restype = None
         L.bf_solve_noalloc.argtypes = [P, P, P, P, P, i64, P, P, P, P, P]
         L.bf_last_error.restype = ctypes.c_char_p
-        for name in ("abs_build", "abs_from_boxes", "abs_export_boxes", "abs_export_pred", "abs_info",
+        for name in ("abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes",
+                     "abs_export_boxes", "abs_export_pred", "abs_info",
                      "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
                      "bf_solve_noalloc"):
             getattr(L, name).restype = ctypes.c_int
@@ -188,6 +192,9 @@ class Abstraction:
                               ctypes.byref(md), ctypes.byref(nb), ctypes.byref(rb)))
         self.ncells, self.ninputs, self.ndim = nc.value, nu.value, nd.value
         self.mode, self.device_bytes, self.box_record_bytes = md.value, nb.value, rb.value
+        k = ctypes.c_int32()
+        _check(lib().abs_stored_inputs(self.handle, ctypes.byref(k)))
+        self.stored_inputs = k.value
 
     def export_boxes(self, out=None, stream=None):
         if out is None:
@@ -213,8 +220,7 @@ class Abstraction:
             pass
 
 
-def abs_build(kind, params, substeps, grid, inputs, tau, mode=MODE_STORED, stream=None):
-    """Build the abstraction of a built-in sampled system on the device."""
+def _system(kind, params, substeps, grid, inputs):
     g = make_grid(grid)
     u = np.ascontiguousarray(np.atleast_2d(inputs), dtype=np.float64)
     inp = Inputs(u.shape[0], u.shape[1], u.ctypes.data)
@@ -223,13 +229,30 @@ def abs_build(kind, params, substeps, grid, inputs, tau, mode=MODE_STORED, strea
     dyn.rk4_substeps = int(substeps)
     for i, p in enumerate(params):
         dyn.param[i] = float(p)
+    return dyn, g, inp, u
+
+
+def abs_build(kind, params, substeps, grid, inputs, tau, mode=MODE_STORED, stream=None):
+    """Build the abstraction of a built-in sampled system on the device."""
+    dyn, g, inp, _keep = _system(kind, params, substeps, grid, inputs)
     h = ctypes.c_void_p()
     _check(lib().abs_build(ctypes.byref(dyn), ctypes.byref(g), ctypes.byref(inp), float(tau), int(mode),
                            _stream(stream), ctypes.byref(h)))
     return Abstraction(h.value, g)
 
 
-def abs_build_workload(w, mode=MODE_STORED, stream=None):
+def abs_build_hybrid(kind, params, substeps, grid, inputs, tau, box_budget, stream=None):
+    """Memory-regulated build: box records of as many inputs as fit box_budget bytes."""
+    dyn, g, inp, _keep = _system(kind, params, substeps, grid, inputs)
+    h = ctypes.c_void_p()
+    _check(lib().abs_build_hybrid(ctypes.byref(dyn), ctypes.byref(g), ctypes.byref(inp), float(tau),
+                                  int(box_budget), _stream(stream), ctypes.byref(h)))
+    return Abstraction(h.value, g)
+
+
+def abs_build_workload(w, mode=MODE_STORED, stream=None, box_budget=None):
+    if box_budget is not None:
+        return abs_build_hybrid(w.kind, w.params, w.substeps, w.grid, w.inputs, w.tau, box_budget, stream)
     return abs_build(w.kind, w.params, w.substeps, w.grid, w.inputs, w.tau, mode, stream)
 
 

@@ -15,6 +15,7 @@
 //              paper notes pred may be replaced by a superset, Sec. V-B).
 // K12 check:   validation of caller-supplied boxes; counts malformed records.
 #include <cstdarg>
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -123,7 +124,7 @@ __global__ void k_import_boxes(GridDesc g, const short* __restrict__ ext, void* 
 
 template <int D>
 __global__ void k_export_boxes(GridDesc g, DynDesc dd, const double* __restrict__ inputs,
-                               const void* __restrict__ boxes, int fmt, short* ext) {
+                               const void* __restrict__ boxes, int fmt, int nstored, short* ext) {
     const long long total = g.C * g.U;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
          p += (long long)gridDim.x * blockDim.x) {
@@ -132,7 +133,7 @@ __global__ void k_export_boxes(GridDesc g, DynDesc dd, const double* __restrict_
         Box<D> b;
         if (fmt == kBoxWide) {
             b = load_box<D>(boxes, p);
-        } else if (fmt == kBoxRecompute) {
+        } else if (fmt == kBoxRecompute || (fmt == kBoxHybrid && u >= nstored)) {
             b = make_box<D>(dd, g, inputs, c, u);
         } else {
             const unsigned long long r = D <= 2 ? reinterpret_cast<const unsigned*>(boxes)[p]
@@ -171,38 +172,66 @@ __global__ void k_export_boxes(GridDesc g, DynDesc dd, const double* __restrict_
 // of dim 0's width byte = the box wraps around a periodic dim for this cell.
 // Sets *fail when some box does not fit the format.
 template <int D>
+__device__ __forceinline__ unsigned long long encode_compact(const GridDesc& g, long long c, const Box<D>& b,
+                                                             bool& bad) {
+    unsigned long long rec = 0;
+    if (b.lo[0] == kBlocked) return 0;
+    int k[4];
+    cell_coords(g, c, k);
+    bool wrap = false;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int n = g.n[d];
+        const int w = b.hi[d] - b.lo[d] + 1;
+        int rel = b.lo[d] - k[d];
+        if (g.periodic[d]) {
+            rel %= n;
+            if (rel < 0) rel += n;
+            if (rel >= n - n / 2) rel -= n;
+            wrap |= (k[d] + rel < 0) || (k[d] + rel + w > n);
+        }
+        bad |= w > 127 || rel < -128 || rel > 127;
+        rec |= (unsigned long long)(unsigned char)(signed char)rel << (16 * d);
+        rec |= (unsigned long long)(w & 0x7F) << (16 * d + 8);
+    }
+    if (wrap) rec |= 0x80ull << 8;
+    return rec;
+}
+
+template <int D>
+__device__ __forceinline__ void store_compact(void* compact, long long p, unsigned long long rec) {
+    if (D <= 2) reinterpret_cast<unsigned*>(compact)[p] = (unsigned)rec;
+    else reinterpret_cast<unsigned long long*>(compact)[p] = rec;
+}
+
+template <int D>
 __global__ void k_to_compact(GridDesc g, const void* __restrict__ wide, void* compact, int* fail) {
     const long long total = g.C * g.U;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
          p += (long long)gridDim.x * blockDim.x) {
         const int u = (int)(p / g.C);
         const long long c = p - (long long)u * g.C;
-        const Box<D> b = load_box<D>(wide, p);
-        unsigned long long rec = 0;
-        if (b.lo[0] != kBlocked) {
-            int k[4];
-            cell_coords(g, c, k);
-            bool wrap = false, bad = false;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int n = g.n[d];
-                const int w = b.hi[d] - b.lo[d] + 1;
-                int rel = b.lo[d] - k[d];
-                if (g.periodic[d]) {
-                    rel %= n;
-                    if (rel < 0) rel += n;
-                    if (rel >= n - n / 2) rel -= n;
-                    wrap |= (k[d] + rel < 0) || (k[d] + rel + w > n);
-                }
-                bad |= w > 127 || rel < -128 || rel > 127;
-                rec |= (unsigned long long)(unsigned char)(signed char)rel << (16 * d);
-                rec |= (unsigned long long)(w & 0x7F) << (16 * d + 8);
-            }
-            if (wrap) rec |= 0x80ull << 8;
-            if (bad) atomicExch(fail, 1);
-        }
-        if (D <= 2) reinterpret_cast<unsigned*>(compact)[p] = (unsigned)rec;
-        else reinterpret_cast<unsigned long long*>(compact)[p] = rec;
+        bool bad = false;
+        const unsigned long long rec = encode_compact<D>(g, c, load_box<D>(wide, p), bad);
+        if (bad) atomicExch(fail, 1);
+        store_compact<D>(compact, p, rec);
+    }
+}
+
+// Boxes of the first g.U inputs built straight into compact records (the
+// hybrid mode's stored part); sets *fail when some box does not fit.
+template <int D>
+__global__ void k_build_compact(DynDesc dd, GridDesc g, const double* __restrict__ inputs, void* compact,
+                                int* fail) {
+    const long long total = g.C * g.U;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long c = p - (long long)u * g.C;
+        bool bad = false;
+        const unsigned long long rec = encode_compact<D>(g, c, make_box<D>(dd, g, inputs, c, u), bad);
+        if (bad) atomicExch(fail, 1);
+        store_compact<D>(compact, p, rec);
     }
 }
 
@@ -500,6 +529,7 @@ extern "C" int abs_build(const bf_dynamics* dyn, const bf_grid* grid, const bf_i
         }
     }
     a->box_fmt = mode == BF_MODE_STORED ? kBoxWide : kBoxRecompute;
+    a->nstored = mode == BF_MODE_STORED ? a->g.U : 0;
     rc = build_pred(a, st);
     if (rc == BF_OK) {
         e = cudaStreamSynchronize(st);
@@ -508,6 +538,65 @@ extern "C" int abs_build(const bf_dynamics* dyn, const bf_grid* grid, const bf_i
     if (rc == BF_OK && mode == BF_MODE_STORED) rc = to_compact(a, st);
     if (rc) { abs_free(a); return rc; }
     *out = a;
+    return BF_OK;
+}
+
+// Memory-regulated build (Sec. IV-B): the recompute-mode abstraction plus the
+// compact records of the first K inputs, K the most whose records fit in
+// box_budget bytes.  K = U gives stored mode, K = 0 (or boxes that do not fit
+// the compact records) recompute mode.
+template <int D>
+static int add_stored_inputs(bf_abstraction* a, int K, cudaStream_t st) {
+    const size_t rec = D <= 2 ? 4 : 8;
+    const size_t bytes = rec * (size_t)a->g.C * K;
+    GridDesc gk = a->g;
+    gk.U = K;
+    void* comp = nullptr;
+    int* d_fail = nullptr;
+    int h_fail = 0;
+    BF_CUDA(cudaMalloc(&comp, bytes));
+    cudaError_t e = cudaMalloc((void**)&d_fail, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_fail, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        DynDesc dd = make_dyndesc(a);
+        k_build_compact<D><<<grid_blocks(gk.C * K, 128), 128, 0, st>>>(dd, gk, a->d_inputs, comp, d_fail);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_fail, d_fail, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_fail);
+    if (e != cudaSuccess) { cudaFree(comp); return bfh::cuda_fail(e, "hybrid box records"); }
+    if (h_fail) { cudaFree(comp); return BF_OK; }      // stays in recompute mode
+    a->d_boxes = comp;
+    a->nstored = K;
+    a->box_fmt = K == a->g.U ? kBoxCompact : kBoxHybrid;
+    a->mode = K == a->g.U ? BF_MODE_STORED : BF_MODE_HYBRID;
+    a->bytes += bytes;
+    return BF_OK;
+}
+
+extern "C" int abs_build_hybrid(const bf_dynamics* dyn, const bf_grid* grid, const bf_inputs* inputs,
+                                double tau, int64_t box_budget, void* stream, bf_abstraction** out) {
+    if (box_budget < 0) { bfh::set_error("abs_build_hybrid: negative budget"); return BF_ERR_INVALID; }
+    int rc = abs_build(dyn, grid, inputs, tau, BF_MODE_RECOMPUTE, stream, out);
+    if (rc) return rc;
+    bf_abstraction* a = *out;
+    const long long rec = a->g.D <= 2 ? 4 : 8;
+    const long long K = std::min<long long>(a->g.U, box_budget / (rec * a->g.C));
+    if (K <= 0) return BF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (a->g.D) {
+        case 2: rc = add_stored_inputs<2>(a, (int)K, st); break;
+        case 3: rc = add_stored_inputs<3>(a, (int)K, st); break;
+        default: rc = add_stored_inputs<4>(a, (int)K, st); break;
+    }
+    if (rc) { abs_free(a); *out = nullptr; }
+    return rc;
+}
+
+extern "C" int abs_stored_inputs(const bf_abstraction* a, int32_t* nstored) {
+    if (!a || !nstored) { bfh::set_error("abs_stored_inputs: NULL argument"); return BF_ERR_INVALID; }
+    *nstored = a->nstored;
     return BF_OK;
 }
 
@@ -562,6 +651,7 @@ extern "C" int abs_from_boxes(const bf_grid* grid, int32_t ninputs, const int16_
         return BF_ERR_INVALID;
     }
     a->box_fmt = kBoxWide;
+    a->nstored = a->g.U;
     rc = build_pred(a, st);
     if (rc == BF_OK) {
         e = cudaStreamSynchronize(st);
@@ -583,10 +673,10 @@ extern "C" int abs_export_boxes(const bf_abstraction* a, int16_t* out, void* str
     DynDesc dd = make_dyndesc(a);
     const int nb = grid_blocks(a->g.C * a->g.U, 128);
     switch (a->g.D) {
-        case 1: k_export_boxes<1><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
-        case 2: k_export_boxes<2><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
-        case 3: k_export_boxes<3><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
-        default: k_export_boxes<4><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, dst); break;
+        case 1: k_export_boxes<1><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, a->nstored, dst); break;
+        case 2: k_export_boxes<2><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, a->nstored, dst); break;
+        case 3: k_export_boxes<3><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, a->nstored, dst); break;
+        default: k_export_boxes<4><<<nb, 128, 0, st>>>(a->g, dd, a->d_inputs, a->d_boxes, a->box_fmt, a->nstored, dst); break;
     }
     BF_CUDA(cudaGetLastError());
     if (!dev) {
@@ -614,7 +704,7 @@ extern "C" int abs_info(const bf_abstraction* a, int64_t* ncells, int32_t* ninpu
     if (mode) *mode = a->mode;
     if (device_bytes) *device_bytes = (int64_t)a->bytes;
     if (box_record_bytes)
-        *box_record_bytes = a->box_fmt == kBoxCompact ? (a->g.D <= 2 ? 4 : 8)
+        *box_record_bytes = (a->box_fmt == kBoxCompact || a->box_fmt == kBoxHybrid) ? (a->g.D <= 2 ? 4 : 8)
                           : a->box_fmt == kBoxWide ? 4 * a->g.D : 0;
     return BF_OK;
 }

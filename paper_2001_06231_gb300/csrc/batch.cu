@@ -208,7 +208,7 @@ __global__ void k_b_cond(const int* active, cudaGraphConditionalHandle h) {
 }
 
 template <int D, int FMT>
-__global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_b_relax(BatchDev b, int g) {
+__global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybrid) ? 2 : 4) k_b_relax(BatchDev b, int g) {
     const int beg = b.gbeg[g], end = b.gbeg[g + 1];
     if (beg >= end) return;
     const int base = b.scan[beg], total = b.scan[end] - base;
@@ -289,7 +289,11 @@ Engine::~Engine() {
 }
 
 size_t Engine::state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, bool stage_V) const {
-    const size_t C = (size_t)a->g.C, U = (size_t)a->g.U, S = (C + 31) / 32;
+    return state_bytes_for(a->g.C, a->g.U, stage_G, stage_T, stage_V);
+}
+
+size_t Engine::state_bytes_for(long long Cc, int Uc, bool stage_G, bool stage_T, bool stage_V) {
+    const size_t C = (size_t)Cc, U = (size_t)Uc, S = (C + 31) / 32;
     size_t o = r256(sizeof(Counters)) + 4 * r256(8 * C) + r256(C) + r256(4 * S) + 2 * r256(4 * C) +
                r256(8 * C * U);
     if (stage_G) o += r256(8 * C * U);
@@ -299,7 +303,7 @@ size_t Engine::state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, 
 }
 
 static int group_of(const bf_abstraction* a) {
-    return (a->g.D - 1) * 3 + a->box_fmt;
+    return (a->g.D - 1) * 4 + a->box_fmt;
 }
 
 int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* target,
@@ -418,9 +422,9 @@ int Engine::rebuild() {
     int ng = 0;
     for (int i = 0; i < n; ++i) {
         const int g = insts_[i]->group;
-        if (ng == 0 || (group_D_[ng - 1] - 1) * 3 + group_fmt_[ng - 1] != g) {
-            group_D_[ng] = g / 3 + 1;
-            group_fmt_[ng] = g % 3;
+        if (ng == 0 || (group_D_[ng - 1] - 1) * 4 + group_fmt_[ng - 1] != g) {
+            group_D_[ng] = g / 4 + 1;
+            group_fmt_[ng] = g % 4;
             dev_.gbeg[ng] = i;
             ++ng;
         }
@@ -465,6 +469,7 @@ static void launch_relax(const BatchDev& b, int g, int fmt, int blocks, cudaStre
     switch (fmt) {
         case kBoxCompact: k_b_relax<D, kBoxCompact><<<blocks, 256, 0, st>>>(b, g); break;
         case kBoxRecompute: k_b_relax<D, kBoxRecompute><<<blocks / 2, 256, 0, st>>>(b, g); break;
+        case kBoxHybrid: k_b_relax<D, kBoxHybrid><<<blocks / 2, 256, 0, st>>>(b, g); break;
         default: k_b_relax<D, kBoxWide><<<blocks, 256, 0, st>>>(b, g); break;
     }
 }

@@ -23,7 +23,7 @@ namespace bfb {
 using bfk::Counters;
 using bfk::InstView;
 
-constexpr int kMaxGroups = 12;  // D in 1..4 x {wide, compact, recompute} boxes
+constexpr int kMaxGroups = 16;  // D in 1..4 x {wide, compact, recompute, hybrid} boxes
 
 // Device-side description of one batch (rebuilt when the instance set changes).
 struct BatchDev {
@@ -80,6 +80,8 @@ public:
     std::vector<InstState*>& list() { return insts_; }
     // Device bytes add() allocates for an instance (upper bound when staging).
     size_t state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, bool stage_V) const;
+    // the same for an instance of C cells and U inputs (before its abstraction exists)
+    static size_t state_bytes_for(long long C, int U, bool stage_G, bool stage_T, bool stage_V);
     cudaStream_t stream() const { return st_; }
 
 private:

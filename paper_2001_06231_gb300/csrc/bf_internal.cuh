@@ -24,6 +24,7 @@ constexpr int16_t kBlocked = -32768;
 constexpr int kBoxWide = 0;      // int16 absolute records [U][C] (4*D bytes)
 constexpr int kBoxCompact = 1;   // int8 relative records [U][C] (4 bytes for D <= 2, else 8)
 constexpr int kBoxRecompute = 2; // not stored: regenerated from the dynamics
+constexpr int kBoxHybrid = 3;    // compact records for inputs u < nstored, recompute for the rest
 constexpr long long kKeyInf = 0x7FF0000000000000LL;   // key(+inf) == bits(+inf)
 constexpr long long kKeyMin = (long long)0x8000000000000000ULL;
 constexpr unsigned char kHandover = 0xFF;
@@ -203,7 +204,8 @@ struct bf_abstraction {
     double* d_inputs;         // [U][udim]
     // stored mode: boxes [U][C], wide (4*D bytes) or compact records
     void* d_boxes;
-    int box_fmt;              // bfk::kBoxWide / kBoxCompact / kBoxRecompute
+    int box_fmt;              // bfk::kBoxWide / kBoxCompact / kBoxRecompute / kBoxHybrid
+    int nstored;              // inputs with stored records (U, 0, or in between: hybrid)
     // predecessor index [C][2*D] int16 offsets (x = y + off), empty: lo0 > hi0
     short* d_pred;
     double pred_rows;         // mean dim-0 rows of a predecessor box (cells with one)

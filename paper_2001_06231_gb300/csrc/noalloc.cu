@@ -138,7 +138,7 @@ __global__ void k_na_tables(InstView v) {
 }
 
 template <int D, int FMT>
-__global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_na_relax(InstView v) {
+__global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybrid) ? 2 : 4) k_na_relax(InstView v) {
     Counters* k = v.ctr;
     if (k->done) return;
     const long long round = k->round;
@@ -217,6 +217,7 @@ int run(const bf_abstraction* a, const InstView& v, const double* G, const unsig
     const int nb = (int)(((C + 255) / 256) < (long long)sms() * 8 ? (C + 255) / 256 : (long long)sms() * 8);
     const int cb = (int)(((S + 255) / 256) < (long long)sms() * 8 ? (S + 255) / 256 : (long long)sms() * 8);
     const int rb = fmt == kBoxRecompute ? wave(k_na_relax<D, kBoxRecompute>)
+                 : fmt == kBoxHybrid ? wave(k_na_relax<D, kBoxHybrid>)
                  : fmt == kBoxCompact ? wave(k_na_relax<D, kBoxCompact>) : wave(k_na_relax<D, kBoxWide>);
     const int pb = wave(k_na_propagate<D>);
     k_na_costs<<<nb, 256, 0, st>>>(C, U, G, avoid, const_cast<double*>(v.Gint), v.ctr);
@@ -235,6 +236,7 @@ int run(const bf_abstraction* a, const InstView& v, const double* G, const unsig
             switch (fmt) {
                 case kBoxCompact: launch_relax<D, kBoxCompact>(v, rb, st); break;
                 case kBoxRecompute: launch_relax<D, kBoxRecompute>(v, rb, st); break;
+                case kBoxHybrid: launch_relax<D, kBoxHybrid>(v, rb, st); break;
                 default: launch_relax<D, kBoxWide>(v, rb, st); break;
             }
             k_na_propagate<D><<<pb, 256, 0, st>>>(v, 1);

@@ -6,8 +6,9 @@
 //   1. admits waiting requests in arrival order while the slot count and the
 //      device-memory budget allow (resolving the request's system to a
 //      resident abstraction, built in STORED mode when its boxes fit the
-//      budget, else in RECOMPUTE mode -- the speed-for-memory trade of
-//      Sec. IV-B), copies their inputs to the device and runs their set-up;
+//      budget, else in HYBRID mode with the records of as many inputs as
+//      fit, else in RECOMPUTE mode -- the memory regulation of Sec. IV-B),
+//      copies their inputs to the device and runs their set-up;
 //   2. runs a bounded number of passes over every admitted request;
 //   3. reads the per-request counters, copies the results of finished
 //      requests to their host buffers and frees their state.
@@ -110,12 +111,9 @@ size_t abs_bytes_estimate(const SystemKey& k, int mode) {
 }
 
 size_t state_bytes_estimate(const SystemKey& k) {
-    size_t C = 1;
-    for (int d = 0; d < k.grid.ndim; ++d) C *= (size_t)k.grid.n[d];
-    const size_t U = (size_t)k.ninputs, S = (C + 31) / 32;
-    // same carve-up as bfb::Engine::add with host inputs and host outputs
-    return 256 + 2 * (8 * C + 256) + (C + 256) + 3 * (4 * S + 256) + (4 * C + 256) + 2 * (8 * C * U + 256) +
-           (8 * C + 256) + 2 * (C + 256) + (8 * C + 256);
+    long long C = 1;
+    for (int d = 0; d < k.grid.ndim; ++d) C *= k.grid.n[d];
+    return bfb::Engine::state_bytes_for(C, k.ninputs, true, true, true);   // as admission counts it
 }
 
 // Find or build the abstraction of a request's system.  Called with the lock
@@ -128,15 +126,26 @@ const bf_abstraction* resolve(bf_server* s, Req* r, std::unique_lock<std::mutex>
         if (c.key.same(r->sys)) return c.a;
     const size_t need_state = state_bytes_estimate(r->sys);
     int mode = -1;
-    if (s->used + abs_bytes_estimate(r->sys, BF_MODE_STORED) + need_state <= s->budget) mode = BF_MODE_STORED;
-    else if (s->used + abs_bytes_estimate(r->sys, BF_MODE_RECOMPUTE) + need_state <= s->budget)
-        mode = BF_MODE_RECOMPUTE;
+    size_t est = 0, box_budget = 0;
+    const size_t base = abs_bytes_estimate(r->sys, BF_MODE_RECOMPUTE);
+    if (s->used + abs_bytes_estimate(r->sys, BF_MODE_STORED) + need_state <= s->budget) {
+        mode = BF_MODE_STORED;
+        est = abs_bytes_estimate(r->sys, BF_MODE_STORED);
+    } else if (s->used + base + need_state <= s->budget) {
+        // store the records of as many inputs as the rest of the budget holds
+        box_budget = s->budget - s->used - base - need_state;
+        size_t C = 1;
+        for (int d = 0; d < r->sys.grid.ndim; ++d) C *= (size_t)r->sys.grid.n[d];
+        const size_t per_input = C * (r->sys.grid.ndim <= 2 ? 4 : 8);
+        const size_t K = std::min<size_t>((size_t)r->sys.ninputs, box_budget / per_input);
+        mode = K > 0 ? BF_MODE_HYBRID : BF_MODE_RECOMPUTE;
+        est = base + K * per_input;
+    }
     if (mode < 0) {
         // fits once other requests leave, unless nothing is running
         *wait = !s->active.empty();
         return nullptr;
     }
-    const size_t est = abs_bytes_estimate(r->sys, mode);
     s->used += est;                     // reserve while building
     lk.unlock();
     bf_inputs in;
@@ -144,7 +153,9 @@ const bf_abstraction* resolve(bf_server* s, Req* r, std::unique_lock<std::mutex>
     in.udim = r->sys.udim;
     in.u = r->sys.inputs.data();
     bf_abstraction* a = nullptr;
-    const int rc = abs_build(&r->sys.dyn, &r->sys.grid, &in, r->sys.tau, mode, s->st, &a);
+    const int rc = mode == BF_MODE_HYBRID
+                       ? abs_build_hybrid(&r->sys.dyn, &r->sys.grid, &in, r->sys.tau, (int64_t)box_budget, s->st, &a)
+                       : abs_build(&r->sys.dyn, &r->sys.grid, &in, r->sys.tau, mode, s->st, &a);
     lk.lock();
     if (rc != BF_OK) {
         s->used -= est;

@@ -159,7 +159,7 @@ __global__ void k_init_counters(Counters* ctr, long long cap) {
 // pass kernels
 // ---------------------------------------------------------------------------
 template <int D, int FMT, bool COUNT, bool MARK>
-__global__ void __launch_bounds__(256, FMT == kBoxRecompute ? 2 : 4) k_relax(InstView v) {
+__global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybrid) ? 2 : 4) k_relax(InstView v) {
     Counters* k = v.ctr;
     if (k->done) return;
     const long long round = k->round;
@@ -351,6 +351,7 @@ static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView&
     switch (a->box_fmt) {
         case kBoxCompact: launch_relax<D, kBoxCompact>(w, v, st, count); break;
         case kBoxRecompute: launch_relax<D, kBoxRecompute>(w, v, st, count); break;
+        case kBoxHybrid: launch_relax<D, kBoxHybrid>(w, v, st, count); break;
         default: launch_relax<D, kBoxWide>(w, v, st, count); break;
     }
     if (tm) { cudaEventRecord(tm->e[1], st); cudaEventRecord(tm->e[2], st); }
@@ -386,6 +387,7 @@ static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
     switch (a->box_fmt) {
         case kBoxCompact: w->relax_blocks = full_wave(k_relax<D, kBoxCompact, false, true>, 256); break;
         case kBoxRecompute: w->relax_blocks = full_wave(k_relax<D, kBoxRecompute, false, true>, 256); break;
+        case kBoxHybrid: w->relax_blocks = full_wave(k_relax<D, kBoxHybrid, false, true>, 256); break;
         default: w->relax_blocks = full_wave(k_relax<D, kBoxWide, false, true>, 256); break;
     }
     w->prop_blocks = full_wave(k_propagate<D>, 256);

@@ -67,7 +67,8 @@ struct Counters {
 struct InstView {
     GridDesc g;
     DynDesc dd;
-    int box_fmt;                // kBoxWide / kBoxCompact / kBoxRecompute
+    int box_fmt;                // kBoxWide / kBoxCompact / kBoxRecompute / kBoxHybrid
+    int nstored;                // hybrid: inputs u < nstored have compact records
     const void* boxes;          // [U][C] records (wide or compact) or NULL
     const double* inputs;       // [U][udim] (recompute mode)
     const short* pred;          // [C][2D] predecessor offsets
@@ -110,6 +111,7 @@ inline void view_from_abs(InstView& v, const bf_abstraction* a) {
         v.dd.eta[d] = d < a->g.D ? (a->ghi[d] - a->glo[d]) / (double)a->g.n[d] : 1.0;
     }
     v.box_fmt = a->box_fmt;
+    v.nstored = a->nstored;
     v.boxes = a->d_boxes;
     v.inputs = a->d_inputs;
     v.pred = a->d_pred;
@@ -484,7 +486,7 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
     s.sig = 0;
     s.wkey = 0;
     if (!act) return;
-    if constexpr (FMT == kBoxCompact) {
+    if (FMT == kBoxCompact || (FMT == kBoxHybrid && u < v.nstored)) {
         const unsigned long long r =
             (unsigned long long)__ldcs(reinterpret_cast<const compact_t<D>*>(v.boxes) + (long long)u * g.C + c);
         const int f0 = rec_byte(r, 1);
@@ -500,7 +502,7 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
         }
     } else {
         Box<D> b;
-        if constexpr (FMT == kBoxRecompute) b = make_box<D>(v.dd, g, v.inputs, c, u);
+        if constexpr (FMT == kBoxRecompute || FMT == kBoxHybrid) b = make_box<D>(v.dd, g, v.inputs, c, u);
         else b = load_box<D>(v.boxes, (long long)u * g.C + c);
         if (b.lo[0] == kBlocked) return;
         s.valid = true;

@@ -22,9 +22,14 @@ def test_batch_equals_solo_mixed_instances():
           wl.unicycle3d(n=(70, 64, 24), n_obstacles=12, seed=2, cost_c=0.7),
           wl.di2d(tau=0.3),
           wl.di2d(),
-          wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0)))]
-    modes = [bf.MODE_STORED, bf.MODE_RECOMPUTE, bf.MODE_STORED, bf.MODE_RECOMPUTE, bf.MODE_STORED]
-    As = [bf.abs_build_workload(w, mode=m) for w, m in zip(ws, modes)]
+          wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0))),
+          wl.unicycle3d(n=(50, 44, 20), n_obstacles=6, seed=3)]
+    modes = [bf.MODE_STORED, bf.MODE_RECOMPUTE, bf.MODE_STORED, bf.MODE_RECOMPUTE, bf.MODE_STORED,
+             bf.MODE_HYBRID]
+    As = [bf.abs_build_workload(w, mode=m) if m != bf.MODE_HYBRID
+          else bf.abs_build_workload(w, box_budget=4 * w.ncells * 8)          # 4 of 10 inputs stored
+          for w, m in zip(ws, modes)]
+    assert As[-1].mode == bf.MODE_HYBRID and As[-1].stored_inputs == 4
     solo = [bf.bf_solve(A, w.G, target=w.target, avoid=w.avoid) for A, w in zip(As, ws)]
     res = bf.bf_solve_batch(As, [w.G for w in ws], targets=[w.target for w in ws],
                             avoids=[w.avoid for w in ws])

@@ -65,18 +65,37 @@ def test_results_alone_equal_results_in_the_mix():
     assert overlapped > 0
 
 
-def test_small_budget_builds_recompute_mode_and_rejects_oversized():
+def test_small_budget_builds_hybrid_or_recompute_mode_and_rejects_oversized():
+    """Sec. IV-B memory control: at the smallest budget that admits the request
+    the server builds a recompute-mode abstraction; with room for the records of
+    3 more inputs it stores those and regenerates the rest (hybrid); results
+    equal a stored-mode solve either way, and a budget below the smallest is
+    refused with BF_ERR_OOM."""
     w = wl.unicycle3d(n=(60, 56, 24), n_obstacles=8)
-    C, U, D = w.ncells, w.ninputs, 3
-    stored_boxes = C * U * 4 * D
-    state = 2 * 8 * C + C + 4 * C + 2 * 8 * C * U + 8 * C + 2 * C + 8 * C + 64 * 1024
-    budget = state + C * 2 * D * 2 + C * D * 8 + stored_boxes // 2     # boxes do not fit, the rest does
-    srv = bf.Server(hbm_budget=budget, max_active=2)
-    rid = srv.submit(w.G, target=w.target, avoid=w.avoid, system=system_of(w))
-    r = srv.poll(rid, wait=True)
-    assert r["error"] == 0 and r["mode"] == bf.MODE_RECOMPUTE
+    C = w.ncells
     s = bf.bf_solve(bf.abs_build_workload(w), w.G, target=w.target, avoid=w.avoid)
-    assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"]) and r["iters"] == s["iters"]
+
+    def serve(budget):
+        srv = bf.Server(hbm_budget=budget, max_active=2)
+        r = srv.poll(srv.submit(w.G, target=w.target, avoid=w.avoid, system=system_of(w)), wait=True)
+        return srv, r
+
+    lo, hi = 1 << 20, 1 << 30                   # refused at lo, admitted at hi
+    while hi - lo > 1024:
+        mid = (lo + hi) // 2
+        srv, r = serve(mid)
+        srv.close()
+        if r["error"] == 0:
+            hi = mid
+        else:
+            assert r["error"] == -2                                  # BF_ERR_OOM
+            lo = mid
+    for budget, mode in ((hi + 1024, bf.MODE_RECOMPUTE), (hi + 1024 + 3 * C * 8, bf.MODE_HYBRID)):
+        srv, r = serve(budget)
+        assert r["error"] == 0 and r["mode"] == mode, (r["error"], r["mode"], mode)
+        assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"]) and r["iters"] == s["iters"]
+        if mode == bf.MODE_RECOMPUTE:
+            srv.close()
     big = wl.unicycle3d(n=(200, 200, 64), n_obstacles=0)
     rid = srv.submit(big.G, target=big.target, system=system_of(big))
     r = srv.poll(rid, wait=True)

@@ -247,3 +247,32 @@ def test_inplace_schedule_builder_workloads(which):
     j = bf.bf_solve(A, w.G, target=w.target, avoid=w.avoid)
     assert j["iters"] == ref["iters"] and same(j["V"], ref["V"]) and same(j["mu"], ref["mu"])
     print("%s: %d in-place passes vs %d Jacobi passes" % (which, r["iters"], ref["iters"]))
+
+
+@pytest.mark.parametrize("which", ["unicycle", "fire"])
+def test_hybrid_mode_is_bit_identical(which):
+    """Memory-regulated builds: the records of the first K inputs are stored, the
+    rest regenerated in relax; boxes and results equal the stored mode's for
+    every K, and device memory grows with K."""
+    if which == "unicycle":
+        w = wl.unicycle3d(n=(60, 50, 24), n_obstacles=8)
+    else:
+        w = wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0)))
+    S = bf.abs_build_workload(w)
+    gb = S.export_boxes()
+    ref = bf.bf_solve(S, w.G, target=w.target, avoid=w.avoid)
+    C, U = w.ncells, w.ninputs
+    rec = 4 if w.grid.ndim <= 2 else 8
+    sizes = []
+    for K in (0, 1, U // 2, U - 1, U):
+        H = bf.abs_build_workload(w, box_budget=K * C * rec + rec * C // 2)
+        assert H.stored_inputs == K
+        assert H.mode == (bf.MODE_RECOMPUTE if K == 0 else bf.MODE_STORED if K == U else bf.MODE_HYBRID)
+        assert same(H.export_boxes(), gb)
+        r = bf.bf_solve(H, w.G, target=w.target, avoid=w.avoid)
+        assert r["iters"] == ref["iters"] and r["status"] == ref["status"]
+        assert same(r["V"], ref["V"]) and same(r["mu"], ref["mu"])
+        sizes.append(H.device_bytes)
+    assert sizes == sorted(sizes) and sizes[0] < sizes[-1]
+    with pytest.raises(bf.BfError):
+        bf.abs_build_workload(w, box_budget=-1)
