@@ -65,6 +65,38 @@ __device__ __forceinline__ void growth_rhs(const double* L, const double* w, con
     }
 }
 
+// One RK4 substep of the centre c and the radius r; inc01 receives the
+// increments added to c[0] and c[1] (the right-hand sides of the built-in
+// systems do not read x[0] and x[1], so these increments depend only on
+// c[2..] and the input).
+template <int D>
+__device__ __forceinline__ void rk4_step(const DynDesc& dd, const double* u, const double* L, const double* w,
+                                         double h, double hh, double h6, double* c, double* r, double* inc01) {
+    double k1[D], k2[D], k3[D], k4[D], t[D];
+    double q1[D], q2[D], q3[D], q4[D], tr[D];
+    dyn_rhs<D>(dd, c, u, k1);
+    growth_rhs<D>(L, w, r, q1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { t[i] = c[i] + hh * k1[i]; tr[i] = r[i] + hh * q1[i]; }
+    dyn_rhs<D>(dd, t, u, k2);
+    growth_rhs<D>(L, w, tr, q2);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { t[i] = c[i] + hh * k2[i]; tr[i] = r[i] + hh * q2[i]; }
+    dyn_rhs<D>(dd, t, u, k3);
+    growth_rhs<D>(L, w, tr, q3);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { t[i] = c[i] + h * k3[i]; tr[i] = r[i] + h * q3[i]; }
+    dyn_rhs<D>(dd, t, u, k4);
+    growth_rhs<D>(L, w, tr, q4);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const double inc = h6 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+        if (i < 2) inc01[i] = inc;
+        c[i] = c[i] + inc;
+        r[i] = r[i] + h6 * (q1[i] + 2.0 * q2[i] + 2.0 * q3[i] + q4[i]);
+    }
+}
+
 template <int D>
 __device__ void rk4_centre_radius(const DynDesc& dd, const double* u, double* c, double* r) {
     double L[D * D], w[D];
@@ -73,28 +105,35 @@ __device__ void rk4_centre_radius(const DynDesc& dd, const double* u, double* c,
     const double hh = h * 0.5, h6 = h / 6.0;
 #pragma unroll 1
     for (int s = 0; s < dd.substeps; ++s) {
-        double k1[D], k2[D], k3[D], k4[D], t[D];
-        double q1[D], q2[D], q3[D], q4[D], tr[D];
-        dyn_rhs<D>(dd, c, u, k1);
-        growth_rhs<D>(L, w, r, q1);
-#pragma unroll
-        for (int i = 0; i < D; ++i) { t[i] = c[i] + hh * k1[i]; tr[i] = r[i] + hh * q1[i]; }
-        dyn_rhs<D>(dd, t, u, k2);
-        growth_rhs<D>(L, w, tr, q2);
-#pragma unroll
-        for (int i = 0; i < D; ++i) { t[i] = c[i] + hh * k2[i]; tr[i] = r[i] + hh * q2[i]; }
-        dyn_rhs<D>(dd, t, u, k3);
-        growth_rhs<D>(L, w, tr, q3);
-#pragma unroll
-        for (int i = 0; i < D; ++i) { t[i] = c[i] + h * k3[i]; tr[i] = r[i] + h * q3[i]; }
-        dyn_rhs<D>(dd, t, u, k4);
-        growth_rhs<D>(L, w, tr, q4);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            c[i] = c[i] + h6 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
-            r[i] = r[i] + h6 * (q1[i] + 2.0 * q2[i] + 2.0 * q3[i] + q4[i]);
-        }
+        double inc01[2];
+        rk4_step<D>(dd, u, L, w, h, hh, h6, c, r, inc01);
     }
+}
+
+// The part of rk4_centre_radius shared by all cells with the same coordinates
+// on dims >= 2 (ckey = their centre there): the dim-0/1 increments of every
+// substep, the final centre on dims >= 2 and the final radius.  A cell's
+// centre on dim 0 or 1 is its start plus the increments, added in order.
+constexpr int kRkMaxSub = 8;
+template <int D>
+__device__ void rk4_shared_part(const DynDesc& dd, const double* u, const double* ckey, double (*inc)[2],
+                                double* cfinal, double* rfinal) {
+    double L[D * D], w[D], c[D], r[D];
+    dyn_growth<D>(dd, u, L, w);
+    const double h = dd.tau / (double)dd.substeps;
+    const double hh = h * 0.5, h6 = h / 6.0;
+    c[0] = 0.0;
+    c[1] = 0.0;
+#pragma unroll
+    for (int d = 2; d < D; ++d) c[d] = ckey[d - 2];
+#pragma unroll
+    for (int d = 0; d < D; ++d) r[d] = dd.eta[d] * 0.5;
+#pragma unroll 1
+    for (int s = 0; s < dd.substeps; ++s) rk4_step<D>(dd, u, L, w, h, hh, h6, c, r, inc[s]);
+#pragma unroll
+    for (int d = 2; d < D; ++d) cfinal[d - 2] = c[d];
+#pragma unroll
+    for (int d = 0; d < D; ++d) rfinal[d] = r[d];
 }
 
 // Cells meeting [a, b] on one dim (half-open cells); false = blocked.
@@ -116,6 +155,22 @@ __device__ __forceinline__ bool quantise_dim(double a, double b, double glo, dou
     lo = (int)m;
     hi = (int)m + (int)len - 1;
     return true;
+}
+
+template <int D>
+__device__ __forceinline__ void quantise_box(const DynDesc& dd, const GridDesc& g, const double* a,
+                                             const double* e, Box<D>& b) {
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        if (ok) ok = quantise_dim(a[d], e[d], dd.glo[d], dd.eta[d], g.n[d], g.periodic[d], b.lo[d], b.hi[d]);
+    if (!ok) {
+        b.lo[0] = kBlocked;
+#pragma unroll
+        for (int d = 1; d < D; ++d) b.lo[d] = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) b.hi[d] = 0;
+    }
 }
 
 template <int D>
@@ -154,17 +209,31 @@ __device__ Box<D> make_box(const DynDesc& dd, const GridDesc& g, const double* _
         b.lo[0] = kBlocked; b.hi[0] = 0;
         return b;
     }
-    bool ok = true;
+    quantise_box<D>(dd, g, a, e, b);
+    return b;
+}
+
+// Box of cell k from the shared part of its (key, input) trajectory: the same
+// operations as make_box, in the same order.
+template <int D>
+__device__ Box<D> box_from_shared(const DynDesc& dd, const GridDesc& g, const int* k, const double (*inc)[2],
+                                  const double* cfinal, const double* rfinal) {
+    Box<D> b;
+    double a[D], e[D], cc[2];
 #pragma unroll
-    for (int d = 0; d < D; ++d)
-        if (ok) ok = quantise_dim(a[d], e[d], dd.glo[d], dd.eta[d], g.n[d], g.periodic[d], b.lo[d], b.hi[d]);
-    if (!ok) {
-        b.lo[0] = kBlocked;
-#pragma unroll
-        for (int d = 1; d < D; ++d) b.lo[d] = 0;
-#pragma unroll
-        for (int d = 0; d < D; ++d) b.hi[d] = 0;
+    for (int d = 0; d < 2; ++d) cc[d] = dd.glo[d] + ((double)k[d] + 0.5) * dd.eta[d];
+#pragma unroll 1
+    for (int s = 0; s < dd.substeps; ++s) {
+        cc[0] = cc[0] + inc[s][0];
+        cc[1] = cc[1] + inc[s][1];
     }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const double c = d < 2 ? cc[d] : cfinal[d - 2];
+        a[d] = c - rfinal[d];
+        e[d] = c + rfinal[d];
+    }
+    quantise_box<D>(dd, g, a, e, b);
     return b;
 }
 
