@@ -84,6 +84,27 @@ __global__ void k_build_boxes(DynDesc dd, GridDesc g, const double* __restrict__
     }
 }
 
+// Shared RK4 parts of every (coordinates on dims >= 2, input) pair for the
+// recompute mode (rk4_shared_part; key = k2 + n2 k3).
+template <int D>
+__global__ void k_rk_table(DynDesc dd, GridDesc g, const double* __restrict__ inputs, long long nkeys,
+                           double* table) {
+    const long long total = nkeys * g.U;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long key = p / g.U;
+        const int u = (int)(p - key * g.U);
+        const int k2 = (int)(key % g.n[2]);
+        const int k3 = (int)(key / g.n[2]);
+        double ckey[2];
+        ckey[0] = dd.glo[2] + ((double)k2 + 0.5) * dd.eta[2];
+        ckey[1] = D >= 4 ? dd.glo[3] + ((double)k3 + 0.5) * dd.eta[3] : 0.0;
+        double* e = table + p * kRkEntry;
+        rk4_shared_part<D>(dd, inputs + (long long)u * dd.udim, ckey, reinterpret_cast<double (*)[2]>(e),
+                           e + 2 * kRkMaxSub, e + 2 * kRkMaxSub + 2);
+    }
+}
+
 // external [C][U][2][D] -> internal [U][C] records, with validation
 template <int D>
 __global__ void k_import_boxes(GridDesc g, const short* __restrict__ ext, void* boxes,
@@ -470,6 +491,7 @@ extern "C" void abs_free(bf_abstraction* a) {
     cudaFree(a->d_boxes);
     cudaFree(a->d_pred);
     cudaFree(a->d_inputs);
+    cudaFree(a->d_rk);
     delete a;
 }
 
@@ -536,6 +558,21 @@ extern "C" int abs_build(const bf_dynamics* dyn, const bf_grid* grid, const bf_i
         if (e != cudaSuccess) rc = bfh::cuda_fail(e, "abs_build kernels");
     }
     if (rc == BF_OK && mode == BF_MODE_STORED) rc = to_compact(a, st);
+    if (rc == BF_OK && mode == BF_MODE_RECOMPUTE && g.D >= 3 && dyn->rk4_substeps <= kRkMaxSub) {
+        // the RK4 work shared by cells with equal coordinates on dims >= 2
+        const long long nkeys = g.C / g.stride[2];
+        const size_t bytes = sizeof(double) * kRkEntry * nkeys * a->g.U;
+        e = cudaMalloc((void**)&a->d_rk, bytes);
+        if (e == cudaSuccess) {
+            const int nb = grid_blocks(nkeys * a->g.U, 64);
+            if (g.D == 3) k_rk_table<3><<<nb, 64, 0, st>>>(dd, a->g, a->d_inputs, nkeys, a->d_rk);
+            else k_rk_table<4><<<nb, 64, 0, st>>>(dd, a->g, a->d_inputs, nkeys, a->d_rk);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = bfh::cuda_fail(e, "recompute RK4 table");
+        else a->bytes += bytes;
+    }
     if (rc) { abs_free(a); return rc; }
     *out = a;
     return BF_OK;

@@ -202,6 +202,7 @@ struct bf_abstraction {
     double tau;
     int udim;
     double* d_inputs;         // [U][udim]
+    double* d_rk;             // recompute / hybrid: shared RK4 parts [keys][U][entry] or NULL
     // stored mode: boxes [U][C], wide (4*D bytes) or compact records
     void* d_boxes;
     int box_fmt;              // bfk::kBoxWide / kBoxCompact / kBoxRecompute / kBoxHybrid

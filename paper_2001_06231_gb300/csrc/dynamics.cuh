@@ -114,7 +114,10 @@ __device__ void rk4_centre_radius(const DynDesc& dd, const double* u, double* c,
 // on dims >= 2 (ckey = their centre there): the dim-0/1 increments of every
 // substep, the final centre on dims >= 2 and the final radius.  A cell's
 // centre on dim 0 or 1 is its start plus the increments, added in order.
+// Table entry layout (kRkEntry doubles): inc[kRkMaxSub][2], cfinal[2],
+// rfinal[4].
 constexpr int kRkMaxSub = 8;
+constexpr int kRkEntry = 2 * kRkMaxSub + 2 + 4;
 template <int D>
 __device__ void rk4_shared_part(const DynDesc& dd, const double* u, const double* ckey, double (*inc)[2],
                                 double* cfinal, double* rfinal) {
@@ -216,25 +219,34 @@ __device__ Box<D> make_box(const DynDesc& dd, const GridDesc& g, const double* _
 // Box of cell k from the shared part of its (key, input) trajectory: the same
 // operations as make_box, in the same order.
 template <int D>
-__device__ Box<D> box_from_shared(const DynDesc& dd, const GridDesc& g, const int* k, const double (*inc)[2],
-                                  const double* cfinal, const double* rfinal) {
+__device__ Box<D> box_from_shared(const DynDesc& dd, const GridDesc& g, const int* k,
+                                  const double* __restrict__ entry) {
     Box<D> b;
     double a[D], e[D], cc[2];
 #pragma unroll
     for (int d = 0; d < 2; ++d) cc[d] = dd.glo[d] + ((double)k[d] + 0.5) * dd.eta[d];
 #pragma unroll 1
     for (int s = 0; s < dd.substeps; ++s) {
-        cc[0] = cc[0] + inc[s][0];
-        cc[1] = cc[1] + inc[s][1];
+        cc[0] = cc[0] + __ldg(entry + 2 * s);
+        cc[1] = cc[1] + __ldg(entry + 2 * s + 1);
     }
+    const double* cfinal = entry + 2 * kRkMaxSub;
+    const double* rfinal = cfinal + 2;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        const double c = d < 2 ? cc[d] : cfinal[d - 2];
-        a[d] = c - rfinal[d];
-        e[d] = c + rfinal[d];
+        const double c = d < 2 ? cc[d] : __ldg(cfinal + d - 2);
+        const double r = __ldg(rfinal + d);
+        a[d] = c - r;
+        e[d] = c + r;
     }
     quantise_box<D>(dd, g, a, e, b);
     return b;
+}
+
+// Index of a cell's shared-RK4 key (its coordinates on dims >= 2).
+template <int D>
+__device__ __forceinline__ int rk_key(const GridDesc& g, const int* k) {
+    return D >= 4 ? k[2] + g.n[2] * k[3] : k[2];
 }
 
 }  // namespace bfk

@@ -107,6 +107,8 @@ size_t abs_bytes_estimate(const SystemKey& k, int mode) {
     size_t b = C * 2 * D * sizeof(short) + U * (size_t)k.udim * 8;   // pred index + inputs
     b += C * D * 8;                                                   // temporary pred bounds
     if (mode == BF_MODE_STORED) b += C * U * 4 * D;                  // boxes
+    else if (D >= 3 && k.dyn.rk4_substeps <= bfk::kRkMaxSub)         // shared RK4 parts
+        b += sizeof(double) * bfk::kRkEntry * U * (C / ((size_t)k.grid.n[0] * k.grid.n[1]));
     return b;
 }
 

@@ -71,6 +71,7 @@ struct InstView {
     int nstored;                // hybrid: inputs u < nstored have compact records
     const void* boxes;          // [U][C] records (wide or compact) or NULL
     const double* inputs;       // [U][udim] (recompute mode)
+    const double* rk;           // [keys][U][kRkEntry] shared RK4 parts (recompute mode) or NULL
     const short* pred;          // [C][2D] predecessor offsets
     const double* Gint;         // [U][C] running cost, +inf on avoid cells
     long long* Vkey;            // [C]
@@ -114,6 +115,7 @@ inline void view_from_abs(InstView& v, const bf_abstraction* a) {
     v.nstored = a->nstored;
     v.boxes = a->d_boxes;
     v.inputs = a->d_inputs;
+    v.rk = a->d_rk;
     v.pred = a->d_pred;
 }
 
@@ -476,26 +478,9 @@ __device__ __forceinline__ int wrap_key(const GridDesc& g, const int* k) {
 
 // k: the cell's coordinates (only read for wrapping boxes and non-compact
 // formats).
-// Recompute mode, built-in systems (right-hand side blind to dims 0 and 1):
-// the lanes of a warp whose cells share their coordinates on dims >= 2 with
-// the warp's first cell share the RK4 work of every input (rk4_shared_part);
-// lane j computes it for input u0 + j into the warp's table, and each lane then
-// rebuilds its box with box_from_shared -- bit-identical to make_box.
-constexpr int kRkMaxIn = 32;
-struct RkTable {
-    double inc[kRkMaxIn][kRkMaxSub][2];
-    double cfinal[kRkMaxIn][2];
-    double rfinal[kRkMaxIn][4];
-};
-struct RkCtx {
-    const RkTable* t;      // NULL: every lane runs make_box
-    int u0;                // input of table slot 0
-    bool mine;             // this lane's cell has the table's key
-};
-
 template <int D, int FMT>
 __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const int* k, int u, bool act,
-                                           PairShape<D>& s, const RkCtx& rk) {
+                                           PairShape<D>& s) {
     const GridDesc& g = v.g;
     s.valid = false;
     s.slow = false;
@@ -520,12 +505,12 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
     } else {
         Box<D> b;
         if constexpr (FMT == kBoxRecompute || FMT == kBoxHybrid) {
-            if (D >= 3 && rk.t && rk.mine) {
-                const int j = u - rk.u0;
-                b = box_from_shared<D>(v.dd, g, k, rk.t->inc[j], rk.t->cfinal[j], rk.t->rfinal[j]);
-            } else {
+            // systems blind to dims 0-1: the abstraction keeps the RK4 work shared
+            // by each (dims >= 2 coordinates, input); bit-identical to make_box
+            if (D >= 3 && v.rk)
+                b = box_from_shared<D>(v.dd, g, k, v.rk + ((long long)rk_key<D>(g, k) * g.U + u) * kRkEntry);
+            else
                 b = make_box<D>(v.dd, g, v.inputs, c, u);
-            }
         } else {
             b = load_box<D>(v.boxes, (long long)u * g.C + c);
         }
@@ -573,42 +558,15 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
     const GridDesc& g = v.g;
     int k[4] = {0, 0, 0, 0};
     if (FMT != kBoxCompact || (g.periodic[0] | g.periodic[1] | g.periodic[2] | g.periodic[3])) cell_coords(g, c, k);
-    RkCtx rk;
-    rk.t = nullptr;
-    rk.u0 = u0;
-    rk.mine = false;
-    if constexpr ((FMT == kBoxRecompute || FMT == kBoxHybrid) && D >= 3) {
-        __shared__ RkTable rk_tab[8];                     // one per warp of a 256-thread block
-        const unsigned am = __ballot_sync(0xFFFFFFFFu, act);
-        if (am && v.dd.substeps <= kRkMaxSub && u1 - u0 <= kRkMaxIn && (threadIdx.x >> 5) < 8) {
-            RkTable* t = &rk_tab[threadIdx.x >> 5];
-            __syncwarp();                                 // the previous chunk's reads are done
-            const int lead = __ffs(am) - 1;
-            int kk[4];
-#pragma unroll
-            for (int d = 0; d < 4; ++d) kk[d] = __shfl_sync(0xFFFFFFFFu, k[d], lead);
-            const int u = u0 + lane;
-            if (u < u1 && (FMT == kBoxRecompute || u >= v.nstored)) {
-                double ckey[2];
-#pragma unroll
-                for (int d = 2; d < D; ++d) ckey[d - 2] = v.dd.glo[d] + ((double)kk[d] + 0.5) * v.dd.eta[d];
-                rk4_shared_part<D>(v.dd, v.inputs + (long long)u * v.dd.udim, ckey, t->inc[lane], t->cfinal[lane],
-                                   t->rfinal[lane]);
-            }
-            __syncwarp();
-            rk.t = t;
-            rk.mine = act && k[2] == kk[2] && k[3] == kk[3];
-        }
-    }
     // the next input's record and cost are loaded while this one is gathered
     PairShape<D> nx;
-    pair_shape<D, FMT>(v, c, k, u0, act, nx, rk);
+    pair_shape<D, FMT>(v, c, k, u0, act, nx);
     double ngv = nx.valid ? __ldcs(v.Gint + (long long)u0 * g.C + c) : 0.0;
     for (int u = u0; u < u1; ++u) {
         PairShape<D> s = nx;
         const double gv = ngv;
         if (u + 1 < u1) {
-            pair_shape<D, FMT>(v, c, k, u + 1, act, nx, rk);
+            pair_shape<D, FMT>(v, c, k, u + 1, act, nx);
             ngv = nx.valid ? __ldcs(v.Gint + (long long)(u + 1) * g.C + c) : 0.0;
         }
         const unsigned vmask = __ballot_sync(0xFFFFFFFFu, s.valid);
