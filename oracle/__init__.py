@@ -57,9 +57,9 @@ def lib():
         L.orc_flow.argtypes = [i32, P, i32, i32, P, f64, P, P]
         L.orc_pred_build.argtypes = [i32, P, P, i32, P, P, ctypes.POINTER(ctypes.c_void_p)]
         L.orc_free.argtypes = [P]
-        L.orc_solve.argtypes = [i32, P, P, i32, P, P, P, P, i64, P, P, P, P, P, P, P, P, i64, P]
+        L.orc_solve.argtypes = [i32, P, P, i32, P, P, P, P, P, P, i64, P, P, P, P, P, P, P, P, i64, P]
         L.orc_dijkstra.argtypes = [i32, P, P, i32, P, P, P, P, P, P]
-        L.orc_bellman_check.argtypes = [i32, P, P, i32, P, P, P, P, P, P, P, i64, P, P]
+        L.orc_bellman_check.argtypes = [i32, P, P, i32, P, P, P, P, P, P, P, P, P, i64, P, P]
         for f in (L.orc_build_boxes, L.orc_flow, L.orc_pred_build, L.orc_solve,
                   L.orc_dijkstra, L.orc_bellman_check):
             f.restype = ctypes.c_int
@@ -125,8 +125,10 @@ def pred(n, periodic, boxes):
     return ptr, col
 
 
-def solve(n, periodic, boxes, G, terminal, avoid=None, max_iters=0, pred_csr=None, trace_cap=None):
-    """Algorithm 1 with Jacobi rounds.
+def solve(n, periodic, boxes, G, terminal, avoid=None, max_iters=0, pred_csr=None, trace_cap=None,
+          succ_class=None, G_class=None):
+    """Algorithm 1 with Jacobi rounds.  succ_class ([C] mask) and G_class
+    ([C][U]) give the running cost G_class(x,u) for successors in the class.
 
     Returns dict(V, mu, iters, status, f1, changed, f1_exit): per-round |F1|
     and number of changed cells, and the F1 mask left when the loop ended.
@@ -139,6 +141,7 @@ def solve(n, periodic, boxes, G, terminal, avoid=None, max_iters=0, pred_csr=Non
     terminal = np.ascontiguousarray(terminal, dtype=np.float64).reshape(C)
     if avoid is not None:
         avoid = np.ascontiguousarray(avoid, dtype=np.uint8).reshape(C)
+    cls, Gc = _class_arrays(succ_class, G_class, C, U)
     V = np.empty(C, dtype=np.float64)
     mu = np.empty(C, dtype=np.uint8)
     iters = np.zeros(1, dtype=np.int64)
@@ -148,7 +151,7 @@ def solve(n, periodic, boxes, G, terminal, avoid=None, max_iters=0, pred_csr=Non
     chg = np.zeros(max(cap, 1), dtype=np.int64)
     ptr, col = (None, None) if pred_csr is None else pred_csr
     f1_exit = np.zeros(C, dtype=np.uint8)
-    _check(lib().orc_solve(D, _p(n), _p(per), U, _p(boxes), _p(G), _p(terminal), _p(avoid),
+    _check(lib().orc_solve(D, _p(n), _p(per), U, _p(boxes), _p(G), _p(terminal), _p(avoid), _p(cls), _p(Gc),
                            int(max_iters), _p(ptr), _p(col), _p(V), _p(mu), _p(iters), _p(status),
                            _p(f1), _p(chg), cap, _p(f1_exit)), "solve")
     it = int(iters[0])
@@ -174,7 +177,14 @@ def dijkstra(n, periodic, boxes, G, terminal, avoid=None):
     return V, mu
 
 
-def bellman_check(n, periodic, boxes, G, terminal, avoid, V, mu, cells=None):
+def _class_arrays(succ_class, G_class, C, U):
+    if succ_class is None:
+        return None, None
+    return (np.ascontiguousarray(succ_class, dtype=np.uint8).reshape(C),
+            np.ascontiguousarray(G_class, dtype=np.float64).reshape(C, U))
+
+
+def bellman_check(n, periodic, boxes, G, terminal, avoid, V, mu, cells=None, succ_class=None, G_class=None):
     """Number of cells violating P(V) = V or mu-attainment; (nbad, first_bad)."""
     n, per = _grid_arrays(n, periodic)
     D = len(n)
@@ -189,7 +199,8 @@ def bellman_check(n, periodic, boxes, G, terminal, avoid, V, mu, cells=None):
     cl = None if cells is None else np.ascontiguousarray(cells, dtype=np.int64)
     nbad = np.zeros(1, dtype=np.int64)
     first = np.zeros(1, dtype=np.int64)
-    _check(lib().orc_bellman_check(D, _p(n), _p(per), U, _p(boxes), _p(G), _p(terminal), _p(avoid),
+    cls, Gc = _class_arrays(succ_class, G_class, C, U)
+    _check(lib().orc_bellman_check(D, _p(n), _p(per), U, _p(boxes), _p(G), _p(terminal), _p(avoid), _p(cls), _p(Gc),
                                    _p(V), _p(mu), _p(cl), 0 if cl is None else len(cl),
                                    _p(nbad), _p(first)), "bellman_check")
     return int(nbad[0]), int(first[0])

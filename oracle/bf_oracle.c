@@ -36,7 +36,12 @@
  *            lo[0] == -32768 marks a box that leaves the grid: its successor
  *            is the overflow set, whose value is +inf (Sec. V-B cover).
  *   G        double [C][U]: the running cost g(x,y,u) = G(x,u) of Eq. (cost)
- *            for every successor y (independent of y).
+ *            for every successor y outside the successor class (below).
+ *   cls, Gc  optional uint8 [C] and double [C][U]: a successor class R (the
+ *            cells with cls[y] != 0) with its own running cost,
+ *            g(x,y,u) = Gc(x,u) for y in R -- the form of g2 in Sec. VI-A
+ *            (a reward -5 tau for successors over the fire, g1 elsewhere).
+ *            NULL: g does not depend on y.
  *   terminal double [C]: the terminal cost G(x) of Eq. (cost).
  *   avoid    uint8 [C] or NULL: an avoid cell x is read as g(x,.,.) = +inf
  *            and g(.,x,.) = +inf with terminal +inf, so it keeps V = +inf.
@@ -413,7 +418,9 @@ void orc_free(void *p) { free(p); }
 struct sup_ctx {
     const double *W;
     const uint8_t *avoid;
-    double g;
+    const uint8_t *cls;
+    double g;      /* g(x,y,u) for y outside the successor class */
+    double gc;     /* g(x,y,u) for y in the successor class      */
     double d;
     int any;
 };
@@ -421,7 +428,8 @@ struct sup_ctx {
 static void sup_visit(int64_t y, void *vctx)
 {
     struct sup_ctx *s = (struct sup_ctx *)vctx;
-    double gy = (s->avoid && s->avoid[y]) ? INFINITY : s->g;   /* g(x,y,u) */
+    double gy = (s->cls && s->cls[y]) ? s->gc : s->g;          /* g(x,y,u) */
+    if (s->avoid && s->avoid[y]) gy = INFINITY;
     double v = gy + s->W[y];
     if (!s->any || v > s->d) s->d = v;
     s->any = 1;
@@ -430,20 +438,22 @@ static void sup_visit(int64_t y, void *vctx)
 /* d(x,u) of Algorithm 1, reading W. */
 static double relax_value(int D, const int32_t *n, const uint8_t *periodic,
                           int U, const int16_t *boxes, const double *G,
+                          const uint8_t *cls, const double *Gc,
                           const uint8_t *avoid, const double *W,
                           int64_t x, int u)
 {
     const int16_t *box = boxes + (x * U + u) * 2 * D;
     if (avoid && avoid[x]) return INFINITY;           /* g(x,.,.) = +inf */
     if (box[0] == ORC_BLOCKED) return INFINITY;       /* overflow set    */
-    struct sup_ctx s = { W, avoid, G[x * U + u], 0.0, 0 };
+    struct sup_ctx s = { W, avoid, cls, G[x * U + u], cls ? Gc[x * U + u] : 0.0, 0.0, 0 };
     for_box(D, n, periodic, box, sup_visit, &s);
     return s.d;
 }
 
 int orc_solve(int D, const int32_t *n, const uint8_t *periodic, int U,
               const int16_t *boxes, const double *G_in, const double *terminal,
-              const uint8_t *avoid, int64_t max_iters,
+              const uint8_t *avoid, const uint8_t *cls, const double *Gc_in,
+              int64_t max_iters,
               const int64_t *pred_ptr, const int32_t *pred_col,
               double *V, uint8_t *mu, int64_t *iters, int32_t *status,
               int64_t *f1_trace, int64_t *chg_trace, int64_t trace_cap,
@@ -454,6 +464,7 @@ int orc_solve(int D, const int32_t *n, const uint8_t *periodic, int U,
     if (check_boxes(D, n, periodic, C, U, boxes) != ORC_OK) return ORC_EINVAL;
 
     double *G = (double *)malloc(sizeof(double) * C * U);
+    double *Gc = cls ? (double *)malloc(sizeof(double) * C * U) : NULL;
     double *Wn = (double *)malloc(sizeof(double) * C);
     uint8_t *inF2 = (uint8_t *)calloc(C, 1);
     int64_t *F1 = (int64_t *)malloc(sizeof(int64_t) * C);
@@ -463,9 +474,12 @@ int orc_solve(int D, const int32_t *n, const uint8_t *periodic, int U,
     int64_t *own_ptr = NULL;
     int32_t *own_col = NULL;
     int rc = ORC_OK;
-    if (!G || !Wn || !inF2 || !F1 || !F2 || !chg || !chmu) { rc = ORC_ENOMEM; goto done; }
+    if (!G || !Wn || !inF2 || !F1 || !F2 || !chg || !chmu || (cls && !Gc)) { rc = ORC_ENOMEM; goto done; }
     for (int64_t p = 0; p < C * U; ++p)
         if (clean_value(G_in[p], &G[p]) != ORC_OK) { rc = ORC_EINVAL; goto done; }
+    if (cls)
+        for (int64_t p = 0; p < C * U; ++p)
+            if (clean_value(Gc_in[p], &Gc[p]) != ORC_OK) { rc = ORC_EINVAL; goto done; }
     if (!pred_ptr) {
         own_ptr = (int64_t *)malloc(sizeof(int64_t) * (C + 1));
         if (!own_ptr) { rc = ORC_ENOMEM; goto done; }
@@ -504,7 +518,7 @@ int orc_solve(int D, const int32_t *n, const uint8_t *periodic, int U,
             double best = V[x];
             int bu = -1;
             for (int u = 0; u < U; ++u) {
-                double d = relax_value(D, n, periodic, U, boxes, G, avoid, V, x, u);
+                double d = relax_value(D, n, periodic, U, boxes, G, cls, Gc, avoid, V, x, u);
                 if (d < best) { best = d; bu = u; }
             }
             if (bu >= 0) { Wn[x] = best; chmu[x] = (uint8_t)bu; chg[nchg++] = x; }
@@ -541,7 +555,7 @@ int orc_solve(int D, const int32_t *n, const uint8_t *periodic, int U,
     else *status = ORC_ITER_CAP;
 
 done:
-    free(G); free(Wn); free(inF2); free(F1); free(F2); free(chg); free(chmu);
+    free(G); free(Gc); free(Wn); free(inF2); free(F1); free(F2); free(chg); free(chmu);
     free(own_ptr); free(own_col);
     return rc;
 }
@@ -694,6 +708,7 @@ out:
 int orc_bellman_check(int D, const int32_t *n, const uint8_t *periodic, int U,
                       const int16_t *boxes, const double *G_in,
                       const double *terminal, const uint8_t *avoid,
+                      const uint8_t *cls, const double *Gc_in,
                       const double *V, const uint8_t *mu,
                       const int64_t *cells, int64_t ncells,
                       int64_t *nbad, int64_t *first_bad)
@@ -703,15 +718,19 @@ int orc_bellman_check(int D, const int32_t *n, const uint8_t *periodic, int U,
     int64_t m = cells ? ncells : C;
     int64_t bad = 0;
     *first_bad = -1;
-    double *Gx = (double *)malloc(sizeof(double) * U);
+    double *Gx = (double *)malloc(sizeof(double) * 2 * U);
     if (!Gx) return ORC_ENOMEM;
+    double *Gcx = Gx + U;
     for (int64_t q = 0; q < m; ++q) {
         int64_t x = cells ? cells[q] : q;
         int ok = 1;
         double t;
         if (clean_value(terminal[x], &t) != ORC_OK) { free(Gx); return ORC_EINVAL; }
-        for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u) {
             if (clean_value(G_in[x * U + u], &Gx[u]) != ORC_OK) { free(Gx); return ORC_EINVAL; }
+            Gcx[u] = 0.0;
+            if (cls && clean_value(Gc_in[x * U + u], &Gcx[u]) != ORC_OK) { free(Gx); return ORC_EINVAL; }
+        }
         if (avoid && avoid[x]) {
             ok = (V[x] == INFINITY) && mu[x] == ORC_HANDOVER;
         } else {
@@ -722,7 +741,7 @@ int orc_bellman_check(int D, const int32_t *n, const uint8_t *periodic, int U,
                 const int16_t *box = boxes + (x * U + u) * 2 * D;
                 double d = INFINITY;
                 if (box[0] != ORC_BLOCKED) {
-                    struct sup_ctx s = { V, avoid, Gx[u], 0.0, 0 };
+                    struct sup_ctx s = { V, avoid, cls, Gx[u], Gcx[u], 0.0, 0 };
                     for_box(D, n, periodic, box, sup_visit, &s);
                     d = s.d;
                 }

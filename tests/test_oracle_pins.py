@@ -166,6 +166,56 @@ def test_brute_force_random_tiny():
     assert checked >= 30
 
 
+def test_successor_class_cost_brute_force():
+    """Running cost that depends on the successor (Sec. VI-A, g2: a reward for
+    successors in a set, another cost elsewhere), g(x,y,u) = Gc(x,u) for y in
+    the class and G(x,u) else.  With non-negative costs the oracle's value is
+    the brute-force value over memoryless controllers and its controller
+    realizes it.  With negative costs it is a fixed point of the dynamic
+    programming operator (Bellman check) no higher than that brute-force value:
+    a cycle of negative cost that the adversary can leave for a dearer
+    successor keeps Algorithm 1's values finite below what any memoryless
+    controller attains (the adversary may also stay in the cycle, and a
+    behaviour that never hands over costs +inf).  With every cell in the class
+    (or none) the cost reduces to the plain Gc (or G)."""
+    rng = np.random.default_rng(11)
+    checked = exact = 0
+    for trial in range(60):
+        nonneg = trial % 3 == 0
+        n, periodic, boxes, G, T = random_tiny(rng, nonneg=nonneg)
+        C, U = boxes.shape[0], boxes.shape[1]
+        cls = (rng.random(C) < 0.4).astype(np.uint8)
+        Gc = rng.integers(0 if nonneg else -4, 3, size=(C, U)).astype(np.float64)
+        r = oracle.solve(n, periodic, boxes, G, T, succ_class=cls, G_class=Gc)
+        if r["status"] == oracle.CONVERGED:
+            F = brute.boxes_to_successors(n, periodic, boxes)
+            gfun = lambda x, y, u: float(Gc[x, u] if cls[y] else G[x, u])
+            Tl = T.tolist()
+            bv = brute.brute_force_value(F, Tl, gfun)
+            if nonneg:
+                assert bv == r["V"].tolist(), trial
+                assert brute.performance(F, Tl, gfun, brute.controller_sets(r["mu"], U)) == r["V"].tolist(), trial
+                exact += 1
+            else:
+                assert all(a <= b for a, b in zip(r["V"].tolist(), bv)), trial
+            nbad, _ = oracle.bellman_check(n, periodic, boxes, G, T, None, r["V"], r["mu"],
+                                           succ_class=cls, G_class=Gc)
+            assert nbad == 0
+            # the check sees a class-blind V as wrong when the class matters
+            plain = oracle.solve(n, periodic, boxes, G, T)
+            if plain["status"] == oracle.CONVERGED and not np.array_equal(plain["V"], r["V"]):
+                nb2, _ = oracle.bellman_check(n, periodic, boxes, G, T, None, plain["V"], plain["mu"],
+                                              succ_class=cls, G_class=Gc)
+                assert nb2 > 0
+            checked += 1
+        for mask, cost in ((np.ones(C, np.uint8), Gc), (np.zeros(C, np.uint8), G)):
+            a = oracle.solve(n, periodic, boxes, G, T, succ_class=mask, G_class=Gc)
+            b = oracle.solve(n, periodic, boxes, cost, T)
+            assert a["status"] == b["status"] and a["iters"] == b["iters"]
+            assert np.array_equal(a["V"], b["V"]) and np.array_equal(a["mu"], b["mu"])
+    assert checked >= 25 and exact >= 12
+
+
 def test_negative_cycle_reported_on_tiny_instances():
     """Instances where the oracle hits the |X| cap must admit a memoryless
     policy whose cost keeps decreasing (no finite brute-force limit reached)."""
