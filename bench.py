@@ -332,7 +332,9 @@ def ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
-        boxes = A.export_boxes()
+        oracle.build()
+        boxes = oracle.build_boxes(w.kind, w.params, w.substeps, w.grid.n, w.grid.lo, w.grid.hi,
+                                   w.grid.periodic, w.inputs, w.tau)          # the oracle's own boxes
         val, sample, _, _, _ = oracle_sample(w, boxes, budget_s=args.cpu_budget)
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + "; " + host_cpu()}
 

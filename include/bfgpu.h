@@ -236,6 +236,13 @@ typedef struct {
                                   (BF_FLAG_COUNT_EXACT, else -1)                  */
     int64_t trace_cap;
     bf_solve_stats *stats;     /* optional output                               */
+    /* Optional successor class (Sec. VI-A, g2: a running cost that depends on
+     * the successor): g(x,y,u) = G_class(x,u) when succ_class[y] != 0, G(x,u)
+     * otherwise.  Both host or device; NULL succ_class = no class.  G_class
+     * follows G's layout and rules ([C][U] double).  Not combined with
+     * BF_FLAG_COUNT_EXACT (BF_ERR_UNSUPPORTED). */
+    const uint8_t *succ_class; /* [C]                                           */
+    const double *G_class;     /* [C][U]                                        */
 } bf_solve_opts;
 
 /* bf_solve -- Algorithm 1 (Sec. IV-A) on the abstraction with running cost G

@@ -69,7 +69,7 @@ class SolveStats(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int64), ("schedule", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("terminal", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
-                ("stats", ctypes.c_void_p)]
+                ("stats", ctypes.c_void_p), ("succ_class", ctypes.c_void_p), ("G_class", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -268,10 +268,16 @@ def abs_from_boxes(grid, boxes, stream=None):
 
 def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0, schedule=SCHED_AUTO,
              host_loop=False, trace_cap=0, V=None, mu=None, stream=None, count_exact=False,
-             time_kernels=False):
-    """Algorithm 1 on the device.  Returns dict(V, mu, iters, status, stats[, trace])."""
+             time_kernels=False, succ_class=None, G_class=None):
+    """Algorithm 1 on the device.  Returns dict(V, mu, iters, status, stats[, trace]).
+
+    succ_class ([C] mask) with G_class ([C][U]): running cost G_class(x,u) for
+    successors in the class, G(x,u) for the others.
+    """
     C = abstraction.ncells
     Gc = _host(G, np.float64)
+    rc_mask = _host(succ_class, np.uint8)
+    rc_cost = _host(G_class, np.float64)
     tg = _host(target, np.uint8)
     av = _host(avoid, np.uint8)
     tm = _host(terminal, np.float64)
@@ -285,6 +291,8 @@ def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0
     opts.flags = ((FLAG_HOST_LOOP if host_loop else 0) | (FLAG_COUNT_EXACT if count_exact else 0)
                   | (FLAG_TIME_KERNELS if time_kernels else 0))
     opts.terminal = _ptr(tm)
+    opts.succ_class = _ptr(rc_mask)
+    opts.G_class = _ptr(rc_cost)
     stats = SolveStats()
     opts.stats = ctypes.addressof(stats)
     trace = None

@@ -61,6 +61,15 @@ struct bf_solve_ws {
     int relax_blocks = 0, prop_blocks = 0, compact_blocks = 0;
     bool fuse_mark = true;          // relax marks F2 (no propagate launch per pass)
     int inplace = 0;                // schedule the views (and the graph) were made for
+    // successor class (allocated on first use)
+    int cls = 0;                    // class in use for the views (and the graph)
+    unsigned char* rmask = nullptr; // [C] device copy of the class mask
+    double* GRint = nullptr;        // [U][C]
+    long long* VN = nullptr;
+    long long* VR = nullptr;
+    long long* M2R = nullptr;
+    long long* M3R = nullptr;
+    double* stage_GR = nullptr;
     std::mutex mtx;
 };
 
@@ -73,6 +82,8 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt); cudaFree(w->stage_avoid);
     cudaFree(w->stage_V); cudaFree(w->trace); cudaFree(w->stamp);
     cudaFree(w->cand_key); cudaFree(w->cand_u); cudaFree(w->slice_cnt);
+    cudaFree(w->rmask); cudaFree(w->GRint); cudaFree(w->VN); cudaFree(w->VR); cudaFree(w->M2R);
+    cudaFree(w->M3R); cudaFree(w->stage_GR);
     delete w;
 }
 
@@ -160,39 +171,7 @@ __global__ void k_init_counters(Counters* ctr, long long cap) {
 // ---------------------------------------------------------------------------
 template <int D, int FMT, bool COUNT, bool MARK>
 __global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybrid) ? 2 : 4) k_relax(InstView v) {
-    Counters* k = v.ctr;
-    if (k->done) return;
-    const long long round = k->round;
-    const int ncur = k->ncur;
-    const int nchunks = (ncur + 31) >> 5;
-    const int wpb = blockDim.x >> 5;
-    const int nwarps = gridDim.x * wpb;
-    const int U = v.g.U;
-    long long relaxed = 0;
-    int exact = 0;
-    // small frontier: split each chunk's inputs over S warps
-    int S = 1, q = U;
-    if (v.cand_key && nchunks > 0 && nchunks < kSliceTarget * nwarps) {
-        S = min(U, (kSliceTarget * nwarps + nchunks - 1) / nchunks);
-        q = (U + S - 1) / S;
-        S = (U + q - 1) / q;
-        if ((long long)nchunks * S * 32 > v.slice_cap) { S = 1; q = U; }
-    }
-    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
-    if (S == 1) {
-        for (int ch = gw; ch < nchunks; ch += nwarps)
-            relaxed += relax_chunk<D, FMT, COUNT, MARK>(v, ch << 5, ncur - (ch << 5), round, &exact);
-    } else {
-        const int items = nchunks * S;
-        for (int it = gw; it < items; it += nwarps) {
-            const int ch = it / S;
-            relaxed += relax_slice<D, FMT, COUNT, MARK>(v, ncur, ch, it - ch * S, S, q, round, &exact);
-        }
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
-        if (COUNT && exact) atomicAdd((unsigned long long*)&k->exact, (unsigned long long)exact);
-    }
+    relax_pass<D, FMT, COUNT, MARK, false>(v);
 }
 
 // Propagate (warp per changed cell): set F2's bits from the changed list
@@ -323,8 +302,18 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.slice_cnt = w->slice_cnt;
     v.slice_cap = w->slice_cap;
     v.inplace = w->inplace;
+    if (w->cls) {
+        v.rmask = w->rmask;
+        v.GRint = w->GRint;
+        v.VN = w->VN;
+        v.VR = w->VR;
+        v.M2R = w->M2R;
+        v.M3R = w->M3R;
+    }
     return v;
 }
+
+void launch_relax_cls(const InstView& v, bool mark, int blocks, cudaStream_t st);   // solve_cls.cu
 
 // Launch one pass: relax, then (unless relax marks the next frontier itself)
 // propagate, then compact (which commits W and closes the pass).  With timing
@@ -348,7 +337,8 @@ template <int D>
 static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
                         cudaGraphConditionalHandle h, int use_graph, bool count, PassTimers* tm) {
     if (tm) cudaEventRecord(tm->e[0], st);
-    switch (a->box_fmt) {
+    if (v.rmask) launch_relax_cls(v, w->fuse_mark, w->relax_blocks, st);
+    else switch (a->box_fmt) {
         case kBoxCompact: launch_relax<D, kBoxCompact>(w, v, st, count); break;
         case kBoxRecompute: launch_relax<D, kBoxRecompute>(w, v, st, count); break;
         case kBoxHybrid: launch_relax<D, kBoxHybrid>(w, v, st, count); break;
@@ -499,10 +489,30 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
         bfh::set_error("bf_solve: unknown schedule %d", sched);
         return BF_ERR_INVALID;
     }
-    if (sched != w->inplace) {
+    const uint8_t* cls_mask = opts ? opts->succ_class : nullptr;
+    const double* cls_cost = opts ? opts->G_class : nullptr;
+    if (cls_mask && !cls_cost) {
+        bfh::set_error("bf_solve: succ_class needs G_class");
+        return BF_ERR_INVALID;
+    }
+    if (cls_mask && opts && (opts->flags & BF_FLAG_COUNT_EXACT)) {
+        bfh::set_error("bf_solve: exact-F1 counting is not combined with a successor class");
+        return BF_ERR_UNSUPPORTED;
+    }
+    const int cls = cls_mask ? 1 : 0;
+    if (sched != w->inplace || cls != w->cls) {
         if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
         if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
         w->inplace = sched;
+        w->cls = cls;
+    }
+    if (cls && !w->VN) {
+        BF_CUDA(cudaMalloc((void**)&w->rmask, C));
+        BF_CUDA(cudaMalloc((void**)&w->GRint, sizeof(double) * C * U));
+        BF_CUDA(cudaMalloc((void**)&w->VN, 8 * C));
+        BF_CUDA(cudaMalloc((void**)&w->VR, 8 * C));
+        BF_CUDA(cudaMalloc((void**)&w->M2R, 8 * C));
+        BF_CUDA(cudaMalloc((void**)&w->M3R, 8 * C));
     }
     // trace buffer (device side), sized to the request
     const long long tcap = (opts && opts->trace) ? opts->trace_cap : 0;
@@ -534,6 +544,13 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     BF_CUDA(cudaMemsetAsync(w->fbits, 0, 4 * w->nwords, st));
     k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dG, (const unsigned char*)dAv,
                                                      w->Gint, w->ctr);
+    if (cls) {
+        const void* dGR;
+        if ((rc = stage_in(cls_cost, sizeof(double) * C * U, (void**)&w->stage_GR, st, &dGR))) return rc;
+        BF_CUDA(cudaMemcpyAsync(w->rmask, cls_mask, C, cudaMemcpyDefault, st));
+        k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dGR, (const unsigned char*)dAv,
+                                                         w->GRint, w->ctr);
+    }
     k_init_values<<<blocks_for(C, 256), 256, 0, st>>>(C, (const double*)dT, (const unsigned char*)dTgt,
                                                       (const unsigned char*)dAv, w->Vkey, w->Vnew, w->mu,
                                                       w->chg, count ? w->stamp : nullptr, w->ctr);

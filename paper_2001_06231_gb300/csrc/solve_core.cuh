@@ -93,6 +93,15 @@ struct InstView {
     int* slice_cnt;             // [slice_cap / 32], zero between passes
     long long slice_cap;
     int inplace;                // BF_SCHED_INPLACE: a decrease is written to Vkey at once
+    // successor class (running cost Gc(x,u) for successors y in the class):
+    // NULL rmask = none.  VN / VR hold V off / on the class (kKeyMin elsewhere),
+    // M2 / M3 then hold VN's windows and M2R / M3R VR's.
+    const unsigned char* rmask; // [C]
+    const double* GRint;        // [U][C] class running cost, +inf on avoid cells
+    long long* VN;
+    long long* VR;
+    long long* M2R;
+    long long* M3R;
 };
 
 // Slices: a pass whose frontier has fewer than kSliceTarget x (warps of the
@@ -173,9 +182,9 @@ __device__ __forceinline__ Box<D> decode_compact(unsigned long long r, const Gri
 // cells), so a box takes ceil(w0/3) x w1 x w2 x w3 lookups.  Lane e computes
 // the offset of lookup e once and the warp walks the offsets broadcast by
 // shuffle, four loads in flight.  Must be called by all 32 lanes.
-template <int D>
+template <int D, bool CLS = false>
 __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c, bool mine,
-                                                  unsigned long long r, long long lc) {
+                                                  unsigned long long r, long long lc, long long* mcls = nullptr) {
     const GridDesc& g = v.g;
     const int lane = threadIdx.x & 31;
     int w[4] = {1, 1, 1, 1}, rel[4] = {0, 0, 0, 0}, k[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
@@ -197,11 +206,15 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
             lo[d] = l;
         }
     }
-    const long long* tab = w[0] == 1 ? v.Vkey : (w[0] == 2 ? v.M2 : v.M3);
+    // successor classes: V off the class in VN / M2 / M3, on it in VR / M2R / M3R
+    const long long* tab = w[0] == 1 ? (CLS ? v.VN : v.Vkey) : (w[0] == 2 ? v.M2 : v.M3);
     const int np = w[0] < 3 ? 1 : (w[0] + 2) / 3;            // lookups per row
     const int total = np * w[1] * w[2] * w[3];
     const long long* p = tab + (mine ? c + rel[0] : 0);
     long long m0 = kKeyMin, m1 = kKeyMin;
+    const long long* pr = nullptr;
+    long long r0 = kKeyMin, r1 = kKeyMin;
+    if constexpr (CLS) pr = (w[0] == 1 ? v.VR : (w[0] == 2 ? v.M2R : v.M3R)) + (mine ? c + rel[0] : 0);
     for (int e0 = 0; e0 < total; e0 += 32) {
         int off = 0;
         const int e = e0 + lane;
@@ -235,13 +248,22 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
                 const long long a0 = __ldg(p + o0), a1 = __ldg(p + o1), a2 = __ldg(p + o2), a3 = __ldg(p + o3);
                 m0 = max(m0, max(a0, a2));
                 m1 = max(m1, max(a1, a3));
+                if constexpr (CLS) {
+                    const long long b0 = __ldg(pr + o0), b1 = __ldg(pr + o1), b2 = __ldg(pr + o2), b3 = __ldg(pr + o3);
+                    r0 = max(r0, max(b0, b2));
+                    r1 = max(r1, max(b1, b3));
+                }
             }
         }
         for (; kk < n; ++kk) {
             const int o = __shfl_sync(0xFFFFFFFFu, off, kk);
-            if (mine) m0 = max(m0, __ldg(p + o));
+            if (mine) {
+                m0 = max(m0, __ldg(p + o));
+                if constexpr (CLS) r0 = max(r0, __ldg(pr + o));
+            }
         }
     }
+    if constexpr (CLS) *mcls = max(r0, r1);
     return max(m0, m1);
 }
 
@@ -551,7 +573,7 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
 // on entry W(c)) and bu (-1, or the lowest input reaching best) are updated
 // on strict decrease; in counting mode in_exact is set when a box holds a
 // cell changed in the previous pass.
-template <int D, int FMT, bool COUNT>
+template <int D, int FMT, bool COUNT, bool CLS = false>
 __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, bool act, int u0, int u1,
                                              long long round, long long& best, int& bu, bool& in_exact) {
     const int lane = threadIdx.x & 31;
@@ -562,16 +584,20 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
     PairShape<D> nx;
     pair_shape<D, FMT>(v, c, k, u0, act, nx);
     double ngv = nx.valid ? __ldcs(v.Gint + (long long)u0 * g.C + c) : 0.0;
+    double ngr = 0.0;
+    if constexpr (CLS) ngr = nx.valid ? __ldcs(v.GRint + (long long)u0 * g.C + c) : 0.0;
     for (int u = u0; u < u1; ++u) {
         PairShape<D> s = nx;
         const double gv = ngv;
+        const double gr = ngr;
         if (u + 1 < u1) {
             pair_shape<D, FMT>(v, c, k, u + 1, act, nx);
             ngv = nx.valid ? __ldcs(v.Gint + (long long)(u + 1) * g.C + c) : 0.0;
+            if constexpr (CLS) ngr = nx.valid ? __ldcs(v.GRint + (long long)(u + 1) * g.C + c) : 0.0;
         }
         const unsigned vmask = __ballot_sync(0xFFFFFFFFu, s.valid);
         if (!vmask) continue;
-        long long m = kKeyMin;
+        long long m = kKeyMin, mr = kKeyMin;
         unsigned todo = __ballot_sync(0xFFFFFFFFu, s.valid && !s.slow);
         if (vmask & ~todo) {                                  // boxes without a relative record
             if (s.valid && s.slow) {
@@ -579,7 +605,12 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
                     s.b = decode_compact<D>(s.sig, g, c);
                     s.have_box = true;
                 }
-                m = box_max<D>(v.Vkey, g, s.b);
+                if constexpr (CLS) {
+                    m = box_max<D>(v.VN, g, s.b);
+                    mr = box_max<D>(v.VR, g, s.b);
+                } else {
+                    m = box_max<D>(v.Vkey, g, s.b);
+                }
             }
         }
         while (todo) {                                        // one row gather per group of equal boxes
@@ -589,8 +620,9 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
             const long long lc = __shfl_sync(0xFFFFFFFFu, (int)c, leader);
             const bool mine = ((todo >> lane) & 1) && s.sig == lsig && s.wkey == lkey;
             todo &= ~__ballot_sync(0xFFFFFFFFu, mine);
-            const long long mm = box_max_rows<D>(v, c, mine, lsig, lc);
-            if (mine) m = mm;
+            long long mmr = kKeyMin;
+            const long long mm = box_max_rows<D, CLS>(v, c, mine, lsig, lc, &mmr);
+            if (mine) { m = mm; mr = mmr; }
         }
         if constexpr (COUNT) {
             if (s.valid && !in_exact) {
@@ -601,9 +633,20 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
                 in_exact = box_has_stamp<D>(v.stamp, g, s.b, (int)round - 1);
             }
         }
-        if (!s.valid || m == kKeyInf) continue;          // +inf + G = +inf
-        const long long dk = key_of(gv + val_of(m));     // the one FP64 add
-        if (dk < best) { best = dk; bu = u; }
+        if constexpr (CLS) {
+            // sup over the box of g(x,y,u) + V(y): G off the class, Gc on it; a part
+            // without cells holds the neutral kKeyMin; fl(g + .) is monotone, so
+            // each part's sup is g + its max
+            if (!s.valid || m == kKeyInf || mr == kKeyInf) continue;
+            long long dk = kKeyMin;
+            if (m != kKeyMin) dk = key_of(gv + val_of(m));
+            if (mr != kKeyMin) dk = max(dk, key_of(gr + val_of(mr)));
+            if (dk < best) { best = dk; bu = u; }
+        } else {
+            if (!s.valid || m == kKeyInf) continue;          // +inf + G = +inf
+            const long long dk = key_of(gv + val_of(m));     // the one FP64 add
+            if (dk < best) { best = dk; bu = u; }
+        }
     }
 }
 
@@ -628,7 +671,7 @@ __device__ __forceinline__ void commit_cell(const InstView& v, long long c, long
 // Returns the number of cells relaxed; in counting mode adds the cells of the
 // exact F1 (some box holds a cell changed in the previous pass) to *exact.
 // MARK: also set the next frontier's bits (no separate propagate launch).
-template <int D, int FMT, bool COUNT, bool MARK = false>
+template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false>
 __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int count, long long round, int* exact) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < count;
@@ -636,7 +679,7 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
     long long best = act ? v.Vkey[c] : 0;
     int bu = -1;
     bool in_exact = false;
-    relax_inputs<D, FMT, COUNT>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
+    relax_inputs<D, FMT, COUNT, CLS>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
     commit_cell<D, COUNT, MARK>(v, c, best, bu, in_exact, exact);
     return count < 32 ? count : 32;
 }
@@ -647,7 +690,7 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
 // smaller candidate -- the same lowest input among the smallest values as one
 // warp going through all inputs -- commits the cells and resets the counter.
 // Returns the cells relaxed (counted by the completing warp).
-template <int D, int FMT, bool COUNT, bool MARK = false>
+template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false>
 __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, int sl, int S, int q, long long round,
                                            int* exact) {
     const int lane = threadIdx.x & 31;
@@ -660,7 +703,7 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
     bool in_exact = false;
     const int u0 = sl * q;
     const int u1 = min(v.g.U, u0 + q);
-    relax_inputs<D, FMT, COUNT>(v, c, act, u0, u1, round, best, bu, in_exact);
+    relax_inputs<D, FMT, COUNT, CLS>(v, c, act, u0, u1, round, best, bu, in_exact);
     const long long base = (long long)ch * S * 32 + lane;
     v.cand_key[base + (long long)sl * 32] = best;
     v.cand_u[base + (long long)sl * 32] = (bu < 0 ? 0xFFFF : bu) | (in_exact ? 1 << 16 : 0);
@@ -686,6 +729,45 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
     return count < 32 ? count : 32;
 }
 
+// One relax launch of the single solve (whole grid): warps take the chunks
+// of 32 frontier cells, or (small frontiers) (chunk, input slice) items.
+template <int D, int FMT, bool COUNT, bool MARK, bool CLS>
+__device__ __forceinline__ void relax_pass(const InstView& v) {
+    Counters* k = v.ctr;
+    if (k->done) return;
+    const long long round = k->round;
+    const int ncur = k->ncur;
+    const int nchunks = (ncur + 31) >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    const int U = v.g.U;
+    long long relaxed = 0;
+    int exact = 0;
+    // small frontier: split each chunk's inputs over S warps
+    int S = 1, q = U;
+    if (v.cand_key && nchunks > 0 && nchunks < kSliceTarget * nwarps) {
+        S = min(U, (kSliceTarget * nwarps + nchunks - 1) / nchunks);
+        q = (U + S - 1) / S;
+        S = (U + q - 1) / q;
+        if ((long long)nchunks * S * 32 > v.slice_cap) { S = 1; q = U; }
+    }
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    if (S == 1) {
+        for (int ch = gw; ch < nchunks; ch += nwarps)
+            relaxed += relax_chunk<D, FMT, COUNT, MARK, CLS>(v, ch << 5, ncur - (ch << 5), round, &exact);
+    } else {
+        const int items = nchunks * S;
+        for (int it = gw; it < items; it += nwarps) {
+            const int ch = it / S;
+            relaxed += relax_slice<D, FMT, COUNT, MARK, CLS>(v, ncur, ch, it - ch * S, S, q, round, &exact);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
+        if (COUNT && exact) atomicAdd((unsigned long long*)&k->exact, (unsigned long long)exact);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // window tables
 // ---------------------------------------------------------------------------
@@ -698,8 +780,15 @@ __device__ __forceinline__ void table_entry(const InstView& v, long long e) {
     const int n0 = g.n[0];
     const long long row = (long long)grid_div(g, 0, (unsigned)e) * n0;
     const int x = (int)(e - row);
+    const bool cls = v.rmask != nullptr;
     const long long m = v.Vnew[e];
-    long long m2 = m, m3 = m;
+    const bool in = cls && v.rmask[e];
+    long long m2 = (cls && in) ? kKeyMin : m, m3 = m2;
+    long long r2 = in ? m : kKeyMin, r3 = r2;
+    if (cls) {
+        v.VN[e] = m2;
+        v.VR[e] = r2;
+    }
     for (int j = 1; j < 3; ++j) {
         int xj = x + j;
         if (xj >= n0) {
@@ -707,11 +796,22 @@ __device__ __forceinline__ void table_entry(const InstView& v, long long e) {
             xj -= n0;
         }
         const long long val = v.Vnew[row + xj];
-        if (j == 1) m2 = max(m2, val);
-        m3 = max(m3, val);
+        const bool inj = cls && v.rmask[row + xj];
+        const long long vn = inj ? kKeyMin : val;
+        if (j == 1) m2 = max(m2, vn);
+        m3 = max(m3, vn);
+        if (cls) {
+            const long long vr = inj ? val : kKeyMin;
+            if (j == 1) r2 = max(r2, vr);
+            r3 = max(r3, vr);
+        }
     }
     v.M2[e] = m2;
     v.M3[e] = m3;
+    if (cls) {
+        v.M2R[e] = r2;
+        v.M3R[e] = r3;
+    }
 }
 
 // Refresh the entries whose window holds the changed cell y (e = y-2 .. y,

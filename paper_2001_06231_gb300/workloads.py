@@ -215,15 +215,16 @@ def fire_intensity(grid, blobs):
 
 def fire4d(n=(100, 100, 36, 8), seed=SEED_BASE + 3, n_blobs=5, n_nofly=6,
            target=((50.0, 250.0), (50.0, 100.0), (-math.radians(10), math.radians(10)), (10.0, 12.5)),
-           sigma=(10.0, 16.0), tau=1.0):
+           sigma=(10.0, 16.0), tau=1.0, extent=1000.0):
     rng = np.random.default_rng(seed)
-    grid = Grid(tuple(n), (0.0, 0.0, -math.pi, 10.0), (1000.0, 1000.0, math.pi, 20.0),
+    grid = Grid(tuple(n), (0.0, 0.0, -math.pi, 10.0), (extent, extent, math.pi, 20.0),
                 (False, False, True, False))
+    f = extent / 1000.0
     inputs = fire_inputs()
     C, U = grid.ncells, inputs.shape[0]
     blobs = []
     for _ in range(n_blobs):
-        bx, by = rng.uniform(150.0, 850.0, size=2)
+        bx, by = rng.uniform(150.0 * f, 850.0 * f, size=2)
         s = rng.uniform(*sigma)
         amp = rng.uniform(0.7, 1.0)
         blobs.append((float(bx), float(by), float(s), float(amp)))
@@ -237,8 +238,8 @@ def fire4d(n=(100, 100, 36, 8), seed=SEED_BASE + 3, n_blobs=5, n_nofly=6,
     avoid = np.zeros(C, dtype=bool)
     nofly = []
     while len(nofly) < n_nofly:
-        cx, cy = rng.uniform(0.0, 1000.0, size=2)
-        sx, sy = rng.uniform(50.0, 200.0, size=2)
+        cx, cy = rng.uniform(0.0, extent, size=2)
+        sx, sy = rng.uniform(50.0 * f, 200.0 * f, size=2)
         ob = [(cx - sx / 2, cx + sx / 2), (cy - sy / 2, cy + sy / 2)]
         if _boxes_meet(ob, list(target[:2])):
             continue
@@ -251,6 +252,23 @@ def fire4d(n=(100, 100, 36, 8), seed=SEED_BASE + 3, n_blobs=5, n_nofly=6,
     return Workload("fire4d", grid, FIRE4D, params, 8, inputs, tau, G,
                     tmask.astype(np.uint8), avoid.astype(np.uint8), seed,
                     {"blobs": blobs, "nofly": nofly, "intensity_min_cost": float(g_cell.min())})
+
+
+def fire4d_fire_cells(w, threshold=0.01, speed=None):
+    """Successor class of the second mission stage (A_fire x A_drop of Sec. VI-A):
+    the cells whose fire intensity at the centre is at least ``threshold`` and,
+    if ``speed`` = (lo, hi) is given, whose speed cell lies inside it.  uint8 [C]."""
+    grid = w.grid
+    I2 = fire_intensity(grid, w.meta["blobs"])
+    n0, n1 = grid.n[0], grid.n[1]
+    rest = grid.ncells // (n0 * n1)
+    mask = np.broadcast_to((I2 >= threshold).reshape(1, n1 * n0), (rest, n1 * n0)).reshape(grid.ncells)
+    if speed is not None:
+        vs = grid.centres(3)
+        vok = (vs >= speed[0]) & (vs <= speed[1])
+        per_v = grid.ncells // grid.n[3]
+        mask = mask & np.repeat(vok, per_v)
+    return np.ascontiguousarray(mask, dtype=np.uint8)
 
 
 def batched(count=64, seed=SEED_BASE + 4, scale=(1.0, 4.0), base=(50, 50, 16)):

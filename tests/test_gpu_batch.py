@@ -13,6 +13,7 @@ import pytest
 import oracle
 import paper_2001_06231_gb300 as bf
 from paper_2001_06231_gb300 import workloads as wl
+from parity import import_boxes, oracle_boxes
 
 pytestmark = pytest.mark.gpu
 
@@ -36,10 +37,15 @@ def test_batch_equals_solo_mixed_instances():
     for r, s in zip(res, solo):
         assert r["iters"] == s["iters"] and r["status"] == s["status"]
         assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"])
-    # one instance also against the oracle directly
-    w, A = ws[1], As[1]
-    ref = oracle.solve(w.grid.n, w.grid.periodic, A.export_boxes(), w.G, w.terminal(), w.avoid)
-    assert np.array_equal(res[1]["V"], ref["V"]) and res[1]["iters"] == ref["iters"]
+    # an instance on the oracle's own boxes, in a batch, against the oracle directly
+    w = ws[1]
+    ob = oracle_boxes(w)
+    Ao = import_boxes(w, ob)
+    rb = bf.bf_solve_batch([Ao, As[0]], [w.G, ws[0].G], targets=[w.target, ws[0].target],
+                           avoids=[w.avoid, ws[0].avoid])
+    ref = oracle.solve(w.grid.n, w.grid.periodic, ob, w.G, w.terminal(), w.avoid)
+    assert np.array_equal(rb[0]["V"], ref["V"]) and np.array_equal(rb[0]["mu"], ref["mu"])
+    assert rb[0]["iters"] == ref["iters"]
 
 
 def test_batch_same_abstraction_many_costs_and_caps():

@@ -1,9 +1,11 @@
 """GPU parity at the measured sizes, in the launch configuration the benchmark
-times (one graph launch per solve, device-resident inputs).
+times (one graph launch per solve, device-resident inputs, compact records).
+Both sides solve the oracle's boxes (imported into the library); the library's
+own builder is compared with the oracle's on every box.
 
-* Unicycle 200 x 200 x 64 x 10 inputs: the oracle solves the exported boxes to
-  the fixed point; V, mu, the pass count, the status and the per-pass changed
-  counts are compared bit for bit, and the Bellman checker runs on every cell.
+* Unicycle 200 x 200 x 64 x 10 inputs: the oracle solves to the fixed point;
+  V, mu, the pass count, the status and the per-pass changed counts are
+  compared bit for bit, and the Bellman checker runs on every cell.
 * Fire model 100 x 100 x 36 x 8 x 15 inputs (tau 2 s): the whole solve is too
   slow for the oracle inside a test, so the oracle replays the first passes
   (cap K, both sides stop with the same state) and the Bellman checker runs on
@@ -18,6 +20,7 @@ import torch
 import oracle
 import paper_2001_06231_gb300 as bf
 from paper_2001_06231_gb300 import workloads as wl
+from parity import import_boxes, mismatches, oracle_boxes
 
 pytestmark = pytest.mark.gpu
 INF = math.inf
@@ -44,9 +47,14 @@ def gpu_solve(A, w, **kw):
 
 def test_unicycle_full_size_bit_exact():
     w = wl.unicycle3d(seed=wl.SEED_BASE + 2)
-    A = bf.abs_build_workload(w)
+    boxes = oracle_boxes(w)
+    own = bf.abs_build_workload(w)
+    mis = mismatches(own.export_boxes(), boxes)
+    print("unicycle 200x200x64: %d of %d boxes differ from the oracle builder" % (mis, boxes.shape[0] * 10))
+    assert mis <= 0.001 * boxes.shape[0] * boxes.shape[1]
+    A = import_boxes(w, boxes)
+    assert A.box_record_bytes == own.box_record_bytes == 8            # the measured record format
     res = gpu_solve(A, w, trace_cap=4096)
-    boxes = A.export_boxes()
     T = w.terminal()
     ref = oracle.solve(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid)
     assert res["status"] == ref["status"] == bf.CONVERGED
@@ -65,8 +73,8 @@ def test_unicycle_full_size_bit_exact():
 
 def test_fire_full_size_prefix_and_bellman():
     w = wl.fire4d(seed=wl.SEED_BASE + 3, tau=2.0, target=FIRE_TARGET)
-    A = bf.abs_build_workload(w)
-    boxes = A.export_boxes()
+    boxes = oracle_boxes(w)
+    A = import_boxes(w, boxes)
     T = w.terminal()
     K = 6
     capped = gpu_solve(A, w, max_iters=K, trace_cap=64)
