@@ -567,6 +567,72 @@ def served(args):
     print(json.dumps(line), flush=True)
 
 
+def mission(args):
+    """The two-stage mission of Sec. VI-A on the fire model: stage 1 flies back
+    to the landing box (running cost tau + phi^2), stage 2 starts from the
+    terminal cost V1 and rewards successors over the fire at drop speed
+    (-5 tau) -- a running cost that depends on the successor.  One step = both
+    solves, V1 handed over on the device."""
+    import torch
+    import paper_2001_06231_gb300 as bf
+    from paper_2001_06231_gb300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w, desc = make_workload("fire4d")
+    C, U = w.ncells, w.ninputs
+    A = bf.abs_build_workload(w)
+    tau = w.tau
+    G1h = np.ascontiguousarray(np.broadcast_to(tau + w.inputs[:, 0] ** 2, (C, U)))
+    fire = wl.fire4d_fire_cells(w, 0.3, speed=(12.5, 16.25))
+    G1 = torch.from_numpy(G1h).to(dev)
+    Gc = torch.full((C, U), -5.0 * tau, dtype=torch.float64, device=dev)
+    cls = torch.from_numpy(fire).to(dev)
+    tg = torch.from_numpy(w.target).to(dev)
+    av = torch.from_numpy(w.avoid).to(dev)
+    V1 = torch.empty(C, dtype=torch.float64, device=dev)
+    mu1 = torch.empty(C, dtype=torch.uint8, device=dev)
+    V2 = torch.empty(C, dtype=torch.float64, device=dev)
+    mu2 = torch.empty(C, dtype=torch.uint8, device=dev)
+    cap = args.mission_cap
+
+    def step(**kw):
+        r1 = bf.bf_solve(A, G1, target=tg, avoid=av, V=V1, mu=mu1, stream=stream, max_iters=cap, **kw)
+        r2 = bf.bf_solve(A, G1, terminal=V1, avoid=av, V=V2, mu=mu2, stream=stream, max_iters=cap,
+                         succ_class=cls, G_class=Gc, **kw)
+        return r1, r2
+
+    c1, c2 = step(count_exact=True)
+    canonical = (c1["stats"]["exact_f1_cells"] + c2["stats"]["exact_f1_cells"]) * U
+    executed = c1["stats"]["executed_pairs"] + c2["stats"]["executed_pairs"]
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(0)
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r1, r2 = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    better = int((V2 < V1).sum().item())
+    line = {"metric": METRIC, "value": canonical / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "two-stage fire mission (Sec. VI-A) on " + desc.replace(", negative costs over fire", "")
+                       + "; stage 1 g = tau + phi^2 to the landing box, stage 2 terminal V1 and g = -5 tau for "
+                       "successors over the fire at 12.5-16.25 m/s (%d cells), tau + phi^2 elsewhere" % int(fire.sum()),
+                       "passes": [r1["iters"], r2["iters"]], "status": [r1["status"], r2["status"]],
+                       "canonical_relaxations_per_step": canonical, "executed_relaxations_per_step": executed,
+                       "cells_where_stage2_beats_V1": better},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -574,7 +640,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="unicycle3d",
-                    choices=["unicycle3d", "fire4d", "di2d", "batched", "served"])
+                    choices=["unicycle3d", "fire4d", "di2d", "batched", "served", "mission"])
+    ap.add_argument("--mission-cap", type=int, default=5000, help="mission: pass cap of each stage")
     ap.add_argument("--requests", type=int, default=600, help="served: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (1/s)")
     ap.add_argument("--payloads", type=int, default=36, help="served: distinct request payloads")
@@ -603,6 +670,8 @@ def main():
         batched(args)
     elif args.workload == "served":
         served(args)
+    elif args.workload == "mission":
+        mission(args)
     else:
         ours(args, rank, world, local_rank)
 

@@ -239,8 +239,7 @@ typedef struct {
     /* Optional successor class (Sec. VI-A, g2: a running cost that depends on
      * the successor): g(x,y,u) = G_class(x,u) when succ_class[y] != 0, G(x,u)
      * otherwise.  Both host or device; NULL succ_class = no class.  G_class
-     * follows G's layout and rules ([C][U] double).  Not combined with
-     * BF_FLAG_COUNT_EXACT (BF_ERR_UNSUPPORTED). */
+     * follows G's layout and rules ([C][U] double). */
     const uint8_t *succ_class; /* [C]                                           */
     const double *G_class;     /* [C][U]                                        */
 } bf_solve_opts;

@@ -313,7 +313,8 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     return v;
 }
 
-void launch_relax_cls(const InstView& v, bool mark, int blocks, cudaStream_t st);   // solve_cls.cu
+void launch_relax_cls(const InstView& v, bool mark, int blocks, cudaStream_t st);         // solve_cls.cu
+void launch_relax_cls_count(const InstView& v, bool mark, int blocks, cudaStream_t st);   // solve_cls_count.cu
 
 // Launch one pass: relax, then (unless relax marks the next frontier itself)
 // propagate, then compact (which commits W and closes the pass).  With timing
@@ -337,7 +338,10 @@ template <int D>
 static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
                         cudaGraphConditionalHandle h, int use_graph, bool count, PassTimers* tm) {
     if (tm) cudaEventRecord(tm->e[0], st);
-    if (v.rmask) launch_relax_cls(v, w->fuse_mark, w->relax_blocks, st);
+    if (v.rmask) {
+        if (count) launch_relax_cls_count(v, w->fuse_mark, w->relax_blocks, st);
+        else launch_relax_cls(v, w->fuse_mark, w->relax_blocks, st);
+    }
     else switch (a->box_fmt) {
         case kBoxCompact: launch_relax<D, kBoxCompact>(w, v, st, count); break;
         case kBoxRecompute: launch_relax<D, kBoxRecompute>(w, v, st, count); break;
@@ -494,10 +498,6 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     if (cls_mask && !cls_cost) {
         bfh::set_error("bf_solve: succ_class needs G_class");
         return BF_ERR_INVALID;
-    }
-    if (cls_mask && opts && (opts->flags & BF_FLAG_COUNT_EXACT)) {
-        bfh::set_error("bf_solve: exact-F1 counting is not combined with a successor class");
-        return BF_ERR_UNSUPPORTED;
     }
     const int cls = cls_mask ? 1 : 0;
     if (sched != w->inplace || cls != w->cls) {
