@@ -256,6 +256,27 @@ BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *t
              const uint8_t *avoid, const bf_solve_opts *opts, double *V, uint8_t *mu,
              int64_t *iters, int32_t *status, void *stream);
 
+/* bf_tune -- pick the pass schedule of this abstraction's solves by timing:
+ * the slice target (inputs of a small frontier's chunks split over warps when
+ * the frontier has fewer chunks than slice_target x warps; 0 = never),
+ * whether relax marks the next frontier itself or a propagate launch does,
+ * and the relax grid (one or half a wave).  Each of the 16 candidates is
+ * solved three times on the given inputs (G, target, avoid and the optional
+ * terminal / succ_class / G_class / max_iters of opts; flags, trace and stats
+ * are ignored); the fastest stays in force for later bf_solve calls on the
+ * handle.  Results never depend on the schedule.  Errors: as bf_solve. */
+typedef struct {
+    int32_t slice_target;
+    int32_t fuse_mark;         /* 1: relax marks the next frontier                */
+    int32_t relax_blocks;
+    int32_t candidates;        /* schedules timed (the default included)          */
+    double best_ms;            /* mean solve time of the chosen schedule          */
+    double default_ms;         /* the same for the default schedule               */
+} bf_tune_result;
+
+BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *target,
+             const uint8_t *avoid, const bf_solve_opts *opts, bf_tune_result *out, void *stream);
+
 /* bf_solve_batch -- n independent instances of bf_solve (possibly on
  * different abstractions of uneven size), advanced together: every device
  * step relaxes the frontiers of all unfinished instances in one launch.

@@ -34,7 +34,7 @@ FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 EXPORTED = ["abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes", "abs_export_boxes",
             "abs_export_pred", "abs_info",
             "abs_free", "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
-            "bf_serve_close", "bf_solve_noalloc", "bf_last_error"]
+            "bf_serve_close", "bf_solve_noalloc", "bf_tune", "bf_last_error"]
 
 
 class BfError(RuntimeError):
@@ -70,6 +70,11 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int64), ("schedule", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("terminal", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
                 ("stats", ctypes.c_void_p), ("succ_class", ctypes.c_void_p), ("G_class", ctypes.c_void_p)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("slice_target", ctypes.c_int32), ("fuse_mark", ctypes.c_int32), ("relax_blocks", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -121,11 +126,12 @@ def lib():
         L.bf_serve_close.argtypes = [P]
         L.bf_serve_close.restype = None
         L.bf_solve_noalloc.argtypes = [P, P, P, P, P, i64, P, P, P, P, P]
+        L.bf_tune.argtypes = [P, P, P, P, P, P, P]
         L.bf_last_error.restype = ctypes.c_char_p
         for name in ("abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes",
                      "abs_export_boxes", "abs_export_pred", "abs_info",
                      "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
-                     "bf_solve_noalloc"):
+                     "bf_solve_noalloc", "bf_tune"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -319,6 +325,26 @@ def _ptr_array(items, conv):
         keep.append(a)
         arr[i] = _ptr(a)
     return arr, keep
+
+
+def bf_tune(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0, stream=None,
+            succ_class=None, G_class=None):
+    """Time the pass schedules of this abstraction on the given inputs and keep the fastest."""
+    Gc = _host(G, np.float64)
+    tg = _host(target, np.uint8)
+    av = _host(avoid, np.uint8)
+    tm = _host(terminal, np.float64)
+    rc_mask = _host(succ_class, np.uint8)
+    rc_cost = _host(G_class, np.float64)
+    opts = SolveOpts()
+    opts.max_iters = int(max_iters)
+    opts.terminal = _ptr(tm)
+    opts.succ_class = _ptr(rc_mask)
+    opts.G_class = _ptr(rc_cost)
+    res = TuneResult()
+    _check(lib().bf_tune(abstraction.handle, _ptr(Gc), _ptr(tg), _ptr(av), ctypes.byref(opts), ctypes.byref(res),
+                         _stream(stream)))
+    return {k: getattr(res, k) for k, _ in res._fields_}
 
 
 def bf_solve_batch(abstractions, Gs, targets=None, avoids=None, terminals=None, max_iters=0, Vs=None,

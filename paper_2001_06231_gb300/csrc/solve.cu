@@ -59,6 +59,9 @@ struct bf_solve_ws {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     int relax_blocks = 0, prop_blocks = 0, compact_blocks = 0;
+    int relax_blocks_full = 0;      // one full wave of the relax kernel
+    int slice_target = kSliceTarget;
+    bool tuned = false;             // bf_tune chose the schedule below
     bool fuse_mark = true;          // relax marks F2 (no propagate launch per pass)
     int inplace = 0;                // schedule the views (and the graph) were made for
     // successor class (allocated on first use)
@@ -301,6 +304,7 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.cand_u = w->cand_u;
     v.slice_cnt = w->slice_cnt;
     v.slice_cap = w->slice_cap;
+    v.slice_target = w->slice_target;
     v.inplace = w->inplace;
     if (w->cls) {
         v.rmask = w->rmask;
@@ -386,8 +390,8 @@ static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
     }
     w->prop_blocks = full_wave(k_propagate<D>, 256);
     // marking inside relax pays when predecessor boxes are small: the marks
-    // then cost less than a separate launch per pass
-    w->fuse_mark = a->pred_rows <= kFuseMarkRows;
+    // then cost less than a separate launch per pass (bf_tune may override)
+    if (!w->tuned) w->fuse_mark = a->pred_rows <= kFuseMarkRows;
     w->compact_blocks = blocks_for(w->nwords, 256);
 }
 
@@ -471,10 +475,11 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
             case 3: set_blocks<3>(a, w); break;
             default: set_blocks<4>(a, w); break;
         }
-        // slice buffers: a sliced pass has nchunks < kSliceTarget x warps and
-        // fewer than 2 x kSliceTarget x warps (chunk, slice) items
+        // slice buffers: a sliced pass has nchunks < slice_target x warps and
+        // fewer than 2 x slice_target x warps (chunk, slice) items
+        w->relax_blocks_full = w->relax_blocks;
         const long long warps = (long long)w->relax_blocks * 8;
-        const long long cap = 2LL * kSliceTarget * warps * 32;
+        const long long cap = 2LL * kSliceTargetMax * warps * 32;
         cudaError_t e = cudaMalloc((void**)&w->cand_key, sizeof(long long) * cap);
         if (e == cudaSuccess) e = cudaMalloc((void**)&w->cand_u, sizeof(int) * cap);
         if (e == cudaSuccess) e = cudaMalloc((void**)&w->slice_cnt, sizeof(int) * (cap / 32));
@@ -623,5 +628,100 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
         o->relax_ms = timed ? relax_ms : 0.0;
         o->propagate_ms = timed ? prop_ms : 0.0;
     }
+    return BF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// schedule tuning
+// ---------------------------------------------------------------------------
+
+// Time one configuration: one warm solve, then the mean of two.
+static int tune_time(const bf_abstraction* a, const double* G, const uint8_t* target, const uint8_t* avoid,
+                     const bf_solve_opts* o, double* V, uint8_t* mu, cudaStream_t st, double* ms) {
+    int64_t iters;
+    int32_t status;
+    int rc = bf_solve(a, G, target, avoid, o, V, mu, &iters, &status, st);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    BF_CUDA(cudaEventCreate(&e0));
+    BF_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && rc == BF_OK; ++r) rc = bf_solve(a, G, target, avoid, o, V, mu, &iters, &status, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / 2.0;
+    return rc;
+}
+
+static void set_schedule(bf_solve_ws* w, int slice_target, bool fuse, int blocks) {
+    std::lock_guard<std::mutex> lock(w->mtx);
+    w->slice_target = slice_target;
+    w->fuse_mark = fuse;
+    w->relax_blocks = blocks;
+    w->tuned = true;
+    if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+    if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
+}
+
+extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* target, const uint8_t* avoid,
+                       const bf_solve_opts* opts, bf_tune_result* out, void* stream) {
+    if (!a || !G || !out) {
+        bfh::set_error("bf_tune: NULL argument");
+        return BF_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    bf_solve_opts o;
+    memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    o.flags = 0;                  // timed as the graph-launched solve
+    o.trace = nullptr;
+    o.trace_cap = 0;
+    o.stats = nullptr;
+    const long long C = a->g.C;
+    double* V = nullptr;
+    uint8_t* mu = nullptr;
+    BF_CUDA(cudaMalloc((void**)&V, 8 * C));
+    cudaError_t e = cudaMalloc((void**)&mu, C);
+    if (e != cudaSuccess) { cudaFree(V); return bfh::cuda_fail(e, "bf_tune buffers"); }
+    // default schedule first (sets up the workspace)
+    double best = 0.0;
+    int rc = tune_time(a, G, target, avoid, &o, V, mu, st, &best);
+    bf_solve_ws* w = a->ws;
+    if (rc == BF_OK && !w) rc = BF_ERR_CUDA;
+    if (rc) { cudaFree(V); cudaFree(mu); return rc; }
+    const int full = w->relax_blocks_full;
+    int b_slice = w->slice_target, b_blocks = w->relax_blocks;
+    bool b_fuse = w->fuse_mark;
+    out->default_ms = best;
+    int tried = 1;
+    const int slices[4] = {0, 1, 2, kSliceTargetMax};
+    for (int si = 0; si < 4 && rc == BF_OK; ++si)
+        for (int f = 0; f < 2 && rc == BF_OK; ++f)
+            for (int bi = 0; bi < 2 && rc == BF_OK; ++bi) {
+                const int blocks = bi == 0 ? full : (full + 1) / 2;
+                set_schedule(w, slices[si], f != 0, blocks);
+                double ms = 0.0;
+                rc = tune_time(a, G, target, avoid, &o, V, mu, st, &ms);
+                ++tried;
+                if (rc == BF_OK && ms < best) {
+                    best = ms;
+                    b_slice = slices[si];
+                    b_fuse = f != 0;
+                    b_blocks = blocks;
+                }
+            }
+    set_schedule(w, b_slice, b_fuse, b_blocks);
+    cudaFree(V);
+    cudaFree(mu);
+    if (rc) return rc;
+    out->slice_target = b_slice;
+    out->fuse_mark = b_fuse ? 1 : 0;
+    out->relax_blocks = b_blocks;
+    out->candidates = tried;
+    out->best_ms = best;
     return BF_OK;
 }

@@ -92,6 +92,7 @@ struct InstView {
     int* cand_u;                // [slice_cap] input (0xFFFF: none) | exact flag << 16
     int* slice_cnt;             // [slice_cap / 32], zero between passes
     long long slice_cap;
+    int slice_target;           // see kSliceTarget
     int inplace;                // BF_SCHED_INPLACE: a decrease is written to Vkey at once
     // successor class (running cost Gc(x,u) for successors y in the class):
     // NULL rmask = none.  VN / VR hold V off / on the class (kKeyMin elsewhere),
@@ -104,9 +105,12 @@ struct InstView {
     long long* M3R;
 };
 
-// Slices: a pass whose frontier has fewer than kSliceTarget x (warps of the
-// relax grid) chunks splits the inputs of each chunk over several warps.
+// Slices: a pass whose frontier has fewer than slice_target x (warps of the
+// relax grid) chunks splits the inputs of each chunk over several warps
+// (slice_target 0: never).  kSliceTarget is the default, kSliceTargetMax the
+// largest a workspace's buffers hold.
 constexpr int kSliceTarget = 2;
+constexpr int kSliceTargetMax = 4;
 
 // Host: the abstraction part of a view (grid, dynamics, boxes, pred).
 inline void view_from_abs(InstView& v, const bf_abstraction* a) {
@@ -745,8 +749,8 @@ __device__ __forceinline__ void relax_pass(const InstView& v) {
     int exact = 0;
     // small frontier: split each chunk's inputs over S warps
     int S = 1, q = U;
-    if (v.cand_key && nchunks > 0 && nchunks < kSliceTarget * nwarps) {
-        S = min(U, (kSliceTarget * nwarps + nchunks - 1) / nchunks);
+    if (v.cand_key && v.slice_target > 0 && nchunks > 0 && nchunks < v.slice_target * nwarps) {
+        S = min(U, (v.slice_target * nwarps + nchunks - 1) / nchunks);
         q = (U + S - 1) / S;
         S = (U + q - 1) / q;
         if ((long long)nchunks * S * 32 > v.slice_cap) { S = 1; q = U; }
