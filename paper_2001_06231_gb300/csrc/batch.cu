@@ -207,7 +207,7 @@ __global__ void k_b_cond(const int* active, cudaGraphConditionalHandle h) {
     cudaGraphSetConditional(h, *active > 0 ? 1 : 0);
 }
 
-template <int D, int FMT>
+template <int D, int FMT, bool MARK>
 __global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybrid) ? 2 : 4) k_b_relax(BatchDev b, int g) {
     const int beg = b.gbeg[g], end = b.gbeg[g + 1];
     if (beg >= end) return;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybri
         const InstView& v = b.views[i];
         const int ch = pos - b.scan[i];
         int exact = 0;
-        const int r = relax_chunk<D, FMT, false>(v, ch << 5, v.ctr->ncur - (ch << 5), v.ctr->round, &exact);
+        const int r = relax_chunk<D, FMT, false, MARK>(v, ch << 5, v.ctr->ncur - (ch << 5), v.ctr->round, &exact);
         if ((threadIdx.x & 31) == 0 && r)
             atomicAdd((unsigned long long*)&v.ctr->relaxed, (unsigned long long)r);
     }
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256, 4) k_b_propagate(BatchDev b, int g) {
         const int pos = base + item;
         const int i = find_instance(b.scan_chg, beg, end, pos);
         const InstView& v = b.views[i];
-        propagate_entry<D>(v, pos - b.scan_chg[i], v.ctr->nchg, true);
+        propagate_entry<D>(v, pos - b.scan_chg[i], v.ctr->nchg, false);      // compact commits
     }
 }
 
@@ -256,7 +256,9 @@ __global__ void __launch_bounds__(256) k_b_compact(BatchDev b) {
     for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < tchg; item += gridDim.x * blockDim.x) {
         const int i = find_instance(b.scan_chg, 0, n, item);
         const InstView& v = b.views[i];
-        refresh_tables(v, v.chg[item - b.scan_chg[i]]);
+        const int y = v.chg[item - b.scan_chg[i]];
+        v.Vkey[y] = v.Vnew[y];                                  // commit W
+        refresh_tables(v, y);
     }
 }
 
@@ -425,9 +427,13 @@ int Engine::rebuild() {
         if (ng == 0 || (group_D_[ng - 1] - 1) * 4 + group_fmt_[ng - 1] != g) {
             group_D_[ng] = g / 4 + 1;
             group_fmt_[ng] = g % 4;
+            group_mark_[ng] = true;
             dev_.gbeg[ng] = i;
             ++ng;
         }
+        // relax marks the next frontier itself when every predecessor box of
+        // the group is small (as in the single solve)
+        if (insts_[i]->a->pred_rows > kFuseMarkRowsBatch) group_mark_[ng - 1] = false;
     }
     dev_.ngroups = ng;
     dev_.gbeg[ng] = n;
@@ -464,14 +470,20 @@ int Engine::rebuild() {
     return BF_OK;
 }
 
-template <int D>
-static void launch_relax(const BatchDev& b, int g, int fmt, int blocks, cudaStream_t st) {
+template <int D, bool MARK>
+static void launch_relax_m(const BatchDev& b, int g, int fmt, int blocks, cudaStream_t st) {
     switch (fmt) {
-        case kBoxCompact: k_b_relax<D, kBoxCompact><<<blocks, 256, 0, st>>>(b, g); break;
-        case kBoxRecompute: k_b_relax<D, kBoxRecompute><<<blocks / 2, 256, 0, st>>>(b, g); break;
-        case kBoxHybrid: k_b_relax<D, kBoxHybrid><<<blocks / 2, 256, 0, st>>>(b, g); break;
-        default: k_b_relax<D, kBoxWide><<<blocks, 256, 0, st>>>(b, g); break;
+        case kBoxCompact: k_b_relax<D, kBoxCompact, MARK><<<blocks, 256, 0, st>>>(b, g); break;
+        case kBoxRecompute: k_b_relax<D, kBoxRecompute, MARK><<<blocks / 2, 256, 0, st>>>(b, g); break;
+        case kBoxHybrid: k_b_relax<D, kBoxHybrid, MARK><<<blocks / 2, 256, 0, st>>>(b, g); break;
+        default: k_b_relax<D, kBoxWide, MARK><<<blocks, 256, 0, st>>>(b, g); break;
     }
+}
+
+template <int D>
+static void launch_relax(const BatchDev& b, int g, int fmt, bool mark, int blocks, cudaStream_t st) {
+    if (mark) launch_relax_m<D, true>(b, g, fmt, blocks, st);
+    else launch_relax_m<D, false>(b, g, fmt, blocks, st);
 }
 
 template <int D>
@@ -481,15 +493,17 @@ static void launch_prop(const BatchDev& b, int g, int blocks, cudaStream_t st) {
 
 void Engine::launch_pass(cudaGraphConditionalHandle h, int use_graph) {
     for (int g = 0; g < dev_.ngroups; ++g) {
+        const bool mark = group_mark_[g];
         switch (group_D_[g]) {
-            case 1: launch_relax<1>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
-            case 2: launch_relax<2>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
-            case 3: launch_relax<3>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
-            default: launch_relax<4>(dev_, g, group_fmt_[g], relax_blocks_, st_); break;
+            case 1: launch_relax<1>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
+            case 2: launch_relax<2>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
+            case 3: launch_relax<3>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
+            default: launch_relax<4>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
         }
     }
     k_b_plan<<<1, 1024, 0, st_>>>(dev_, 1, h, use_graph);
     for (int g = 0; g < dev_.ngroups; ++g) {
+        if (group_mark_[g]) continue;                        // relax marked the next frontier
         switch (group_D_[g]) {
             case 1: launch_prop<1>(dev_, g, prop_blocks_, st_); break;
             case 2: launch_prop<2>(dev_, g, prop_blocks_, st_); break;

@@ -24,6 +24,7 @@ using bfk::Counters;
 using bfk::InstView;
 
 constexpr int kMaxGroups = 16;  // D in 1..4 x {wide, compact, recompute, hybrid} boxes
+constexpr double kFuseMarkRowsBatch = 64.0;   // mean predecessor-box rows up to which relax marks
 
 // Device-side description of one batch (rebuilt when the instance set changes).
 struct BatchDev {
@@ -94,6 +95,7 @@ private:
     size_t dev_mem_bytes_ = 0;
     int relax_blocks_ = 0, prop_blocks_ = 0, compact_blocks_ = 0;
     int group_D_[kMaxGroups] = {}, group_fmt_[kMaxGroups] = {};
+    bool group_mark_[kMaxGroups] = {};   // relax marks the next frontier (no propagate launch)
 };
 
 }  // namespace bfb
