@@ -334,6 +334,7 @@ def ours(args, rank, world, local_rank):
                 traffic = None
 
     cpu = None
+    builder_mismatch = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         oracle.build()
@@ -341,6 +342,10 @@ def ours(args, rank, world, local_rank):
                                    w.grid.periodic, w.inputs, w.tau)          # the oracle's own boxes
         val, sample, _, _, _ = oracle_sample(w, boxes, budget_s=args.cpu_budget)
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + "; " + host_cpu()}
+        if A.mode == bf.MODE_STORED:
+            # the library's builder against the oracle's, box by box
+            gb = A.export_boxes()
+            builder_mismatch = int(np.any(gb != boxes, axis=(2, 3)).sum())
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -351,7 +356,8 @@ def ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (boxes %d MB + G %d MB > 129 MB)" % (
                        C * U * A.box_record_bytes >> 20, w.G.nbytes >> 20),
                    "abs_build_ms": build_s * 1e3, "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "schedule": tuned},
+                   "schedule": tuned,
+                   "builder_boxes_differing_from_oracle": builder_mismatch},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_relax",
                      "peak_source": peak_src, "relax_ms_per_launch": relax_ms_avg,
