@@ -2,9 +2,11 @@
 // instances (each with its own abstraction, costs, target and avoid set;
 // uneven sizes) advanced together.  A pass is one relax launch per group of
 // instances sharing dimension and storage mode, one planning launch, one
-// propagate launch per group and one finishing launch; each launch covers
-// every unfinished instance, its warps pulling (instance, segment) or
-// (instance, changed cell) work items through per-instance prefix offsets.
+// propagate launch per group whose predecessor boxes are too large for relax
+// to mark the next frontier itself, one compaction launch (which also commits
+// W) and one finishing launch; each launch covers every unfinished instance,
+// its warps pulling (instance, 32-cell chunk) or (instance, changed cell) work
+// items through per-instance prefix offsets.
 // Instances keep their own pass counters, frontiers and termination, so each
 // result is identical to a solo bf_solve.
 //
