@@ -179,6 +179,7 @@ void engine_loop(bf_server* s) {
     for (;;) {
         std::vector<std::pair<Req*, const bf_abstraction*>> admit;
         std::vector<Req*> failed;
+        bool waiting = false;               // requests left in the queue after admission
         {
             std::unique_lock<std::mutex> lk(s->m);
             s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
@@ -208,6 +209,7 @@ void engine_loop(bf_server* s) {
                 r->res.mode = a->mode;
                 admit.push_back({r, a});
             }
+            waiting = !s->pending.empty();
         }
         bool changed = false;
         for (auto& pa : admit) {
@@ -236,7 +238,9 @@ void engine_loop(bf_server* s) {
         }
         if (changed) s->eng->rebuild();
         if (s->eng->list().empty()) continue;
-        s->eng->step(s->passes);
+        // with nobody waiting for a slot, longer steps cost no admission delay and
+        // save host round trips; arrivals then wait at most one longer step
+        s->eng->step(waiting ? s->passes : 4 * s->passes);
         if (s->eng->read_counters(ctrs) != BF_OK) {
             // a CUDA error: fail every active request
             std::lock_guard<std::mutex> lk(s->m);
