@@ -198,13 +198,23 @@ __global__ void __launch_bounds__(1024) k_b_plan(BatchDev b, int mode, cudaGraph
         block_exclusive_scan(b.scan, n, sums);
         if (t == 0) {
             *b.active = active;
-            if (use_graph) cudaGraphSetConditional(h, active > 0 ? 1 : 0);
+            if (use_graph) {
+                int cont = active > 0 ? 1 : 0;
+                if (use_graph == 2) cont = cont && (--*b.step_left > 0);   // bounded step
+                cudaGraphSetConditional(h, cont);
+            }
         }
     }
 }
 
 __global__ void k_b_cond(const int* active, cudaGraphConditionalHandle h) {
     cudaGraphSetConditional(h, *active > 0 ? 1 : 0);
+}
+
+// First node of a bounded step: `passes` passes at most, none when all are done.
+__global__ void k_b_step_init(int* step_left, const int* active, int passes, cudaGraphConditionalHandle h) {
+    *step_left = passes;
+    cudaGraphSetConditional(h, (*active > 0 && passes > 0) ? 1 : 0);
 }
 
 template <int D, int FMT, bool MARK>
@@ -280,7 +290,31 @@ static int blocks_for(long long work) {
 
 static size_t r256(size_t b) { return (b + 255) & ~size_t(255); }
 
+Engine::Engine(cudaStream_t st) : st_(st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pool_, &props) == cudaSuccess) {
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+        pool_ = nullptr;                    // fall back to the device's default pool
+        cudaGetLastError();
+    }
+}
+
+int Engine::alloc(void** p, size_t bytes) {
+    if (pool_) BF_CUDA(cudaMallocFromPoolAsync(p, bytes, pool_, st_));
+    else BF_CUDA(cudaMallocAsync(p, bytes, st_));
+    return BF_OK;
+}
+
 Engine::~Engine() {
+    drop_step_graphs();
     for (InstState* s : insts_) {
         cudaFreeAsync(s->mem, st_);
         delete s;
@@ -288,6 +322,7 @@ Engine::~Engine() {
     insts_.clear();
     if (dev_mem_) cudaFreeAsync(dev_mem_, st_);
     cudaStreamSynchronize(st_);
+    if (pool_) cudaMemPoolDestroy(pool_);
 }
 
 size_t Engine::state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, bool stage_V) const {
@@ -341,7 +376,7 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
     const size_t o_sav = o;  o += sAv ? r256((size_t)C) : 0;
     const size_t o_sv = o;   o += vdev ? 0 : r256(8 * (size_t)C);
     void* mem = nullptr;
-    BF_CUDA(cudaMallocAsync(&mem, o, st_));
+    if (int rc = alloc(&mem, o)) return rc;
     unsigned char* m = static_cast<unsigned char*>(mem);
     InstState* s = new InstState;
     s->a = a;
@@ -437,11 +472,12 @@ int Engine::rebuild() {
     }
     dev_.ngroups = ng;
     dev_.gbeg[ng] = n;
-    const size_t need = r256(sizeof(InstView) * std::max(n, 1)) + 3 * r256(4 * (size_t)(n + 1)) + r256(4);
+    drop_step_graphs();
+    const size_t need = r256(sizeof(InstView) * std::max(n, 1)) + 3 * r256(4 * (size_t)(n + 1)) + 2 * r256(4);
     if (need > dev_mem_bytes_) {
         if (dev_mem_) BF_CUDA(cudaFreeAsync(dev_mem_, st_));
         dev_mem_ = nullptr;
-        BF_CUDA(cudaMallocAsync(&dev_mem_, need, st_));
+        if (int rc = alloc(&dev_mem_, need)) return rc;
         dev_mem_bytes_ = need;
     }
     unsigned char* m = static_cast<unsigned char*>(dev_mem_);
@@ -454,6 +490,8 @@ int Engine::rebuild() {
     dev_.scan_cmp = reinterpret_cast<int*>(m);
     m += r256(4 * (size_t)(n + 1));
     dev_.active = reinterpret_cast<int*>(m);
+    m += r256(4);
+    dev_.step_left = reinterpret_cast<int*>(m);
     host_views_.resize(n);
     for (int i = 0; i < n; ++i) host_views_[i] = insts_[i]->view;
     if (n)
@@ -563,10 +601,83 @@ int Engine::run_to_completion() {
     return BF_OK;
 }
 
-int Engine::step(int passes) {
-    if (dev_.n == 0) return BF_OK;
-    for (int p = 0; p < passes; ++p) launch_pass(0, 0);
-    BF_CUDA(cudaGetLastError());
+void Engine::drop_step_graphs() {
+    for (int i = 0; i < 2; ++i) {
+        if (step_exec_[i]) cudaGraphExecDestroy(step_exec_[i]);
+        step_exec_[i] = nullptr;
+        step_passes_[i] = 0;
+    }
+}
+
+int Engine::build_step_graph(int passes, cudaGraphExec_t* out) {
+    cudaGraph_t graph;
+    BF_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return bfh::cuda_fail(e, "step graph handle"); }
+    cudaGraphNode_t n0;
+    {
+        int* left = dev_.step_left;
+        const int* act = dev_.active;
+        void* args[] = {(void*)&left, (void*)&act, (void*)&passes, (void*)&h};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void*)k_b_step_init;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&n0, graph, nullptr, 0, &kp);
+        if (e != cudaSuccess) { cudaGraphDestroy(graph); return bfh::cuda_fail(e, "step graph node"); }
+    }
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t nc;
+    e = cudaGraphAddNode(&nc, graph, &n0, nullptr, 1, &cp);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return bfh::cuda_fail(e, "step graph loop"); }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return bfh::cuda_fail(e, "step graph stream"); }
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaStream_t keep = st_;
+        st_ = cs;
+        launch_pass(h, 2);
+        st_ = keep;
+        cudaGraph_t captured;
+        e = cudaStreamEndCapture(cs, &captured);
+    }
+    cudaStreamDestroy(cs);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfh::cuda_fail(e, "step graph");
+    return BF_OK;
+}
+
+int Engine::step(int passes, bool graph) {
+    if (dev_.n == 0 || passes <= 0) return BF_OK;
+    if (!graph) {
+        for (int p = 0; p < passes; ++p) launch_pass(0, 0);
+        BF_CUDA(cudaGetLastError());
+        return BF_OK;
+    }
+    int slot = -1;
+    for (int i = 0; i < 2; ++i)
+        if (step_exec_[i] && step_passes_[i] == passes) slot = i;
+    if (slot < 0) {
+        slot = step_exec_[0] ? (step_exec_[1] ? 0 : 1) : 0;
+        if (step_exec_[slot]) cudaGraphExecDestroy(step_exec_[slot]);
+        step_exec_[slot] = nullptr;
+        const int rc = build_step_graph(passes, &step_exec_[slot]);
+        if (rc) return rc;
+        step_passes_[slot] = passes;
+    }
+    BF_CUDA(cudaGraphLaunch(step_exec_[slot], st_));
     return BF_OK;
 }
 

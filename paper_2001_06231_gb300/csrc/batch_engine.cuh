@@ -35,6 +35,7 @@ struct BatchDev {
     int* scan_chg;      // [n + 1] exclusive prefix of the changed cells
     int* scan_cmp;      // [n + 1] exclusive prefix of the 256-word compaction chunks
     int* active;        // [1] unfinished instances
+    int* step_left;     // [1] passes left in a bounded engine step (graph form)
     int n;
     int ngroups;
     int gbeg[kMaxGroups + 1];   // instances of group g are [gbeg[g], gbeg[g + 1])
@@ -61,7 +62,7 @@ struct InstState {
 // Engine: owns the device batch description and launches passes.
 class Engine {
 public:
-    explicit Engine(cudaStream_t st) : st_(st) {}
+    explicit Engine(cudaStream_t st);
     ~Engine();
     // Set up an instance (allocate state, stage inputs, run lines 1-10 of
     // Algorithm 1).  Inputs may be host or device.  Returns BF_OK or an error.
@@ -72,8 +73,10 @@ public:
     int rebuild();
     // Run passes until every instance is done (graph with a WHILE node).
     int run_to_completion();
-    // Run at most `passes` passes (host loop); returns BF_OK.
-    int step(int passes);
+    // Run at most `passes` passes: host-launched, or (graph) one launch of a
+    // WHILE node bounded by a device pass counter, kept until the instance set
+    // changes (worth it when the set is stable for several steps).
+    int step(int passes, bool graph = false);
     // Copy the results of finished instances out; fills *iters/*status.
     int finish_instance(InstState* s, int64_t* iters, int32_t* status, int* err);
     // Remove an instance (frees its state).
@@ -90,6 +93,11 @@ public:
 private:
     void launch_pass(cudaGraphConditionalHandle h, int use_graph);
     cudaStream_t st_;
+    // stream-ordered pool of the per-instance state; it keeps freed memory
+    // (release threshold: unbounded) so that instances joining later reuse it
+    // instead of mapping new memory
+    cudaMemPool_t pool_ = nullptr;
+    int alloc(void** p, size_t bytes);
     std::vector<InstState*> insts_;
     std::vector<InstView> host_views_;   // kept alive until the async copy is done
     BatchDev dev_{};
@@ -98,6 +106,11 @@ private:
     int relax_blocks_ = 0, prop_blocks_ = 0, compact_blocks_ = 0;
     int group_D_[kMaxGroups] = {}, group_fmt_[kMaxGroups] = {};
     bool group_mark_[kMaxGroups] = {};   // relax marks the next frontier (no propagate launch)
+    // bounded-step graphs of the current instance set, by pass count
+    cudaGraphExec_t step_exec_[2] = {nullptr, nullptr};
+    int step_passes_[2] = {0, 0};
+    void drop_step_graphs();
+    int build_step_graph(int passes, cudaGraphExec_t* out);
 };
 
 }  // namespace bfb

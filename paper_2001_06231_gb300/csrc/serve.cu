@@ -240,7 +240,8 @@ void engine_loop(bf_server* s) {
         if (s->eng->list().empty()) continue;
         // with nobody waiting for a slot, longer steps cost no admission delay and
         // save host round trips; arrivals then wait at most one longer step
-        s->eng->step(waiting ? s->passes : 4 * s->passes);
+        if (waiting) s->eng->step(s->passes);        // the set changes often: host-launched passes
+        else s->eng->step(4 * s->passes, true);    // light load: one graph launch per step
         if (s->eng->read_counters(ctrs) != BF_OK) {
             // a CUDA error: fail every active request
             std::lock_guard<std::mutex> lk(s->m);
