@@ -430,6 +430,14 @@ def batched(args):
     torch.cuda.synchronize()
     seq_s = e0.elapsed_time(e1) / 1e3 / args.steps
     n = len(ws)
+    # the batched results are the solo results, bit for bit
+    solo = [(V.clone(), mu.clone()) for V, mu in zip(Vs, mus)]
+    rb = batch_step()
+    torch.cuda.synchronize()
+    identical = all(torch.equal(V, sv) and torch.equal(mu, sm) for V, mu, (sv, sm) in zip(Vs, mus, solo))
+    identical = identical and [r["iters"] for r in rb] == passes
+    if not identical:
+        raise SystemExit("batched results differ from the solo solves")
     line = {"metric": METRIC, "value": canonical / batch_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": batch_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -440,7 +448,7 @@ def batched(args):
                        "executed_relaxations_per_step": executed, "abs_build_ms": build_s * 1e3},
             "queries_per_s": n / batch_s, "sequential_queries_per_s": n / seq_s,
             "sequential_ms_per_step": seq_s * 1e3, "batched_over_sequential": seq_s / batch_s,
-            "clocks": clocks}
+            "batched_identical_to_solo": identical, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

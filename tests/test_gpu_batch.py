@@ -77,3 +77,16 @@ def test_batch_rejects_nan_instance():
     G[5, 2] = np.nan
     with pytest.raises(bf.BfError):
         bf.bf_solve_batch([A, A], [w.G, G], targets=[w.target, w.target], avoids=[w.avoid, w.avoid])
+
+
+def test_batch_full_size_64_uneven_unicycles():
+    """The measured batch: 64 unicycle instances of uneven size (44 M cells in
+    all) in one bf_solve_batch, each identical to its solo solve."""
+    ws = wl.batched(count=64)
+    As = [bf.abs_build_workload(w) for w in ws]
+    solo = [bf.bf_solve(A, w.G, target=w.target, avoid=w.avoid) for A, w in zip(As, ws)]
+    res = bf.bf_solve_batch(As, [w.G for w in ws], targets=[w.target for w in ws],
+                            avoids=[w.avoid for w in ws])
+    for r, s in zip(res, solo):
+        assert r["iters"] == s["iters"] and r["status"] == s["status"]
+        assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"])
