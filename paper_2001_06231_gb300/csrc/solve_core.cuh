@@ -447,6 +447,11 @@ __device__ __forceinline__ void mark_changed(const InstView& v, int y, bool chan
     const bool cont = has && lane > 0 && hprev && y == yprev + 1 && ky[0] != 0;
     const unsigned contm = __ballot_sync(0xFFFFFFFFu, cont);
     unsigned heads = __ballot_sync(0xFFFFFFFFu, has && !cont);
+    // the previous run's box: when this run's box is the same box moved up by
+    // one cell on dim 1 (and no wider on dim 0), the previous box -- marked by
+    // this warp -- holds all of it but its top row on dim 1
+    int plo[4] = {0, 0, 0, 0}, plen[4] = {0, 0, 0, 0};
+    bool prev = false;
     while (heads) {
         const int h = __ffs(heads) - 1;
         heads &= heads - 1;
@@ -470,6 +475,25 @@ __device__ __forceinline__ void mark_changed(const InstView& v, int y, bool chan
             lo[d] = s;
             len[d] = len_d;
             if (d > 0) rows *= len_d;
+        }
+        if constexpr (D >= 2) {
+            bool covered = prev && !g.periodic[0] && plo[0] <= lo[0] && plo[0] + plen[0] >= lo[0] + len[0] &&
+                           plen[1] == len[1] && len[1] < g.n[1];
+            int up = plo[1] + 1;
+            if (g.periodic[1] && up >= g.n[1]) up -= g.n[1];
+            covered = covered && up == lo[1];
+#pragma unroll
+            for (int d = 2; d < D; ++d) covered = covered && plo[d] == lo[d] && plen[d] == len[d];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) { plo[d] = lo[d]; plen[d] = len[d]; }
+            prev = true;
+            if (covered) {                                    // only the top row on dim 1
+                int top = lo[1] + len[1] - 1;
+                if (g.periodic[1] && top >= g.n[1]) top -= g.n[1];
+                lo[1] = top;
+                rows /= len[1];
+                len[1] = 1;
+            }
         }
         mark_box_rows<D>(v, lo, len, rows);
     }
