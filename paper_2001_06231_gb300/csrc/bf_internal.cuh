@@ -71,6 +71,21 @@ inline void grid_divisors(GridDesc& g) {
 __device__ __forceinline__ unsigned grid_div(const GridDesc& g, int d, unsigned x) {
     return (__umulhi(g.dmul[d], x) + x) >> g.dshr[d];
 }
+
+// Quotients t / d of box extents (1 <= d <= 255, 0 <= t < 2^23) by one
+// multiply-high: with m = ceil(2^31 / d), m d = 2^31 + e and 0 <= e < d, so
+// umulhi(2t, m) = floor(t m / 2^31) = floor(t / d + t e / (d 2^31)); writing
+// t = q d + r (r <= d - 1), t e < 2^23 * 254 < 2^31 keeps r + t e / 2^31 below
+// d and the floor at q.
+struct RecipTable { unsigned m[256]; };
+constexpr RecipTable make_recip_table() {
+    RecipTable r{};
+    for (unsigned d = 1; d < 256; ++d) r.m[d] = (unsigned)((0x80000000ull + d - 1) / d);
+    return r;
+}
+static __constant__ RecipTable kRecip = make_recip_table();
+constexpr unsigned kSmallDivMax = 1u << 23;
+__device__ __forceinline__ unsigned small_div(unsigned t, unsigned m) { return __umulhi(t << 1, m); }
 #endif
 
 // Box of one (cell, input) pair in registers.

@@ -214,6 +214,10 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
     const long long* tab = w[0] == 1 ? (CLS ? v.VN : v.Vkey) : (w[0] == 2 ? v.M2 : v.M3);
     const int np = w[0] < 3 ? 1 : (w[0] + 2) / 3;            // lookups per row
     const int total = np * w[1] * w[2] * w[3];
+    // lookup e = q + np (j1 + w1 (j2 + w2 j3)); below 2^23 lookups (every box
+    // of a real system) its digits come from multiply-high quotients
+    const bool quick = (unsigned)total < kSmallDivMax;
+    const unsigned inv_q = kRecip.m[np], inv_1 = kRecip.m[w[1]], inv_2 = kRecip.m[w[2]];
     const long long* p = tab + (mine ? c + rel[0] : 0);
     long long m0 = kKeyMin, m1 = kKeyMin;
     const long long* pr = nullptr;
@@ -223,14 +227,32 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
         int off = 0;
         const int e = e0 + lane;
         if (e < total) {
-            int t = e;
-            const int q = t % np;
-            t /= np;
-            int j[4];
-            j[1] = t % w[1];
-            t /= w[1];
-            j[2] = t % w[2];
-            j[3] = t / w[2];
+            int q, j[4] = {0, 0, 0, 0};
+            if (quick) {
+                const unsigned t1 = small_div((unsigned)e, inv_q);
+                q = e - (int)(t1 * np);
+                if constexpr (D == 2) {
+                    j[1] = (int)t1;
+                } else if constexpr (D >= 3) {
+                    const unsigned t2 = small_div(t1, inv_1);
+                    j[1] = (int)(t1 - t2 * w[1]);
+                    if constexpr (D == 3) {
+                        j[2] = (int)t2;
+                    } else {
+                        const unsigned t3 = small_div(t2, inv_2);
+                        j[2] = (int)(t2 - t3 * w[2]);
+                        j[3] = (int)t3;
+                    }
+                }
+            } else {
+                int t = e;
+                q = t % np;
+                t /= np;
+                j[1] = t % w[1];
+                t /= w[1];
+                j[2] = t % w[2];
+                j[3] = t / w[2];
+            }
             off = w[0] < 3 ? 0 : min(3 * q, w[0] - 3);
 #pragma unroll
             for (int d = 1; d < D; ++d) {
@@ -320,18 +342,21 @@ __device__ __forceinline__ void mark_box_rows(const InstView& v, const int* lo, 
     const int a0 = lo[0], e0 = lo[0] + len[0] - 1;
     const int e1 = min(e0, n0 - 1);
     const bool wrap = e0 >= n0;                                   // periodic dim 0: the part past n0 - 1 wraps
+    // row r = j1 + len1 (j2 + len2 j3): multiply-high quotients for the usual sizes
+    const bool quick = (unsigned)rows < kSmallDivMax && len[1] < 256 && (D < 4 || len[2] < 256);
+    const unsigned m1 = kRecip.m[min(len[1], 255)], m2 = kRecip.m[min(len[2], 255)];
     for (int r = lane; r < rows; r += 32) {
         int j[4] = {0, 0, 0, 0};
         const unsigned t = (unsigned)r;
-        if (D == 2) {
+        if constexpr (D == 2) {
             j[1] = (int)t;
-        } else if (D == 3) {
-            j[2] = (int)(t / (unsigned)len[1]);
+        } else if constexpr (D == 3) {
+            j[2] = (int)(quick ? small_div(t, m1) : t / (unsigned)len[1]);
             j[1] = (int)(t - (unsigned)j[2] * (unsigned)len[1]);
-        } else if (D == 4) {
-            const unsigned t2 = t / (unsigned)len[1];
+        } else if constexpr (D == 4) {
+            const unsigned t2 = quick ? small_div(t, m1) : t / (unsigned)len[1];
             j[1] = (int)(t - t2 * (unsigned)len[1]);
-            j[3] = (int)(t2 / (unsigned)len[2]);
+            j[3] = (int)(quick ? small_div(t2, m2) : t2 / (unsigned)len[2]);
             j[2] = (int)(t2 - (unsigned)j[3] * (unsigned)len[2]);
         }
         int rowbase = 0;
@@ -409,9 +434,10 @@ __device__ __forceinline__ void propagate_entry(const InstView& v, int i, int nc
         if (a > b) return;                                        // no predecessor in the run
         int s = kh[d] + a;
         int len_d = b - a + 1;
-        if (g.periodic[d]) {
+        if (g.periodic[d]) {                      // s in [-n/2, 3n/2): offsets are kept in [-n/2, n/2)
             if (len_d >= n) { s = 0; len_d = n; }
-            else { s %= n; if (s < 0) s += n; }
+            else if (s < 0) s += n;
+            else if (s >= n) s -= n;
         }
         lo[d] = s;
         len[d] = len_d;
@@ -459,7 +485,7 @@ __device__ __forceinline__ void mark_changed(const InstView& v, int y, bool chan
         const int last = h + __ffs(~above) - 1;          // the run is lanes h..last
         const bool in = lane >= h && lane <= last;
         int lo[4] = {0, 0, 0, 0}, len[4] = {1, 1, 1, 1};
-        int rows = 1;
+        int rows = 1, rows2 = 1;                          // rows2: product of len[2..D-1]
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int n = g.n[d];
@@ -468,13 +494,15 @@ __device__ __forceinline__ void mark_changed(const InstView& v, int y, bool chan
             const int mx = __reduce_max_sync(0xFFFFFFFFu, in ? base + qh[d] : (int)0x80000000);
             int s = mn + (d == 0 ? 0 : __shfl_sync(0xFFFFFFFFu, ky[d], h));
             int len_d = mx - mn + 1;
-            if (g.periodic[d]) {
+            if (g.periodic[d]) {                  // s in [-n/2, 3n/2): offsets are kept in [-n/2, n/2)
                 if (len_d >= n) { s = 0; len_d = n; }
-                else { s %= n; if (s < 0) s += n; }
+                else if (s < 0) s += n;
+                else if (s >= n) s -= n;
             }
             lo[d] = s;
             len[d] = len_d;
             if (d > 0) rows *= len_d;
+            if (d > 1) rows2 *= len_d;
         }
         if constexpr (D >= 2) {
             bool covered = prev && !g.periodic[0] && plo[0] <= lo[0] && plo[0] + plen[0] >= lo[0] + len[0] &&
@@ -491,7 +519,7 @@ __device__ __forceinline__ void mark_changed(const InstView& v, int y, bool chan
                 int top = lo[1] + len[1] - 1;
                 if (g.periodic[1] && top >= g.n[1]) top -= g.n[1];
                 lo[1] = top;
-                rows /= len[1];
+                rows = rows2;
                 len[1] = 1;
             }
         }

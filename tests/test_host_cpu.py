@@ -96,3 +96,20 @@ def test_grid_division_by_multiply_high_is_exact():
         for x in (k - np.uint64(1), k):
             q = (((x * np.uint64(m)) >> np.uint64(32)) + x) >> np.uint64(l)
             assert np.array_equal(q, x // np.uint64(n)), n
+
+
+def test_box_extent_division_by_multiply_high_is_exact():
+    """Gather and marking split a lookup or row index t by box extents d with
+    m = ceil(2^31 / d) and t // d = mulhi(2t, m) for 1 <= d <= 255 and
+    t < 2^23: checked for every d on every t near a multiple of d (where an
+    off-by-one would show) up to 2^23, and on every t below 2^16."""
+    import numpy as np
+    top = np.uint64(1 << 23)
+    small = np.arange(0, 1 << 16, dtype=np.uint64)
+    for d in range(1, 256):
+        m = np.uint64(((1 << 31) + d - 1) // d)
+        k = np.arange(1, (1 << 23) // d + 2, dtype=np.uint64) * np.uint64(d)
+        ts = np.concatenate([small, k - np.uint64(1), k, top - np.uint64(1 + np.arange(4, dtype=np.uint64))])
+        ts = ts[ts < top]
+        q = ((ts << np.uint64(1)) * m) >> np.uint64(32)
+        assert np.array_equal(q, ts // np.uint64(d)), d
