@@ -260,7 +260,10 @@ BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *t
  * the slice target (inputs of a small frontier's chunks split over warps when
  * the frontier has fewer chunks than slice_target x warps; 0 = never),
  * whether relax marks the next frontier itself or a propagate launch does,
- * and the relax grid (one or half a wave).  Each of the 16 candidates is
+ * the relax grid (one or half a wave) and, on grids of 2 or more dims,
+ * whether boxes at least 3 cells wide on dims 0 and 1 read a table of 3 x 3
+ * window maxima (fewer gathers, more table upkeep per changed cell).  Each of
+ * the 16 (32) candidates is
  * solved three times on the given inputs (G, target, avoid and the optional
  * terminal / succ_class / G_class / max_iters of opts; flags, trace and stats
  * are ignored); the fastest stays in force for later bf_solve calls on the
@@ -272,10 +275,20 @@ typedef struct {
     int32_t candidates;        /* schedules timed (the default included)          */
     double best_ms;            /* mean solve time of the chosen schedule          */
     double default_ms;         /* the same for the default schedule               */
+    int32_t window33;          /* 1: the 3 x 3 window table is used               */
 } bf_tune_result;
 
 BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *target,
              const uint8_t *avoid, const bf_solve_opts *opts, bf_tune_result *out, void *stream);
+
+/* bf_set_schedule -- put a pass schedule in force without timing (a schedule
+ * bf_tune printed earlier, or a fixed one): slice_target 0..4, fuse_mark,
+ * relax_blocks (<= 0 or above one wave: one wave) and window33 of *sched are
+ * read, the rest ignored; window33 has no effect on 1-D grids or solves with
+ * a successor class.  Results never depend on the schedule.  Returns BF_OK,
+ * BF_ERR_INVALID (NULL argument, slice_target out of range) or BF_ERR_CUDA /
+ * BF_ERR_OOM (the handle's solve workspace could not be set up). */
+BF_API int bf_set_schedule(const bf_abstraction *abs, const bf_tune_result *sched, void *stream);
 
 /* bf_solve_batch -- n independent instances of bf_solve (possibly on
  * different abstractions of uneven size), advanced together: every device

@@ -34,7 +34,7 @@ FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 EXPORTED = ["abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes", "abs_export_boxes",
             "abs_export_pred", "abs_info",
             "abs_free", "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
-            "bf_serve_close", "bf_solve_noalloc", "bf_tune", "bf_last_error"]
+            "bf_serve_close", "bf_solve_noalloc", "bf_tune", "bf_set_schedule", "bf_last_error"]
 
 
 class BfError(RuntimeError):
@@ -74,7 +74,8 @@ class SolveOpts(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("slice_target", ctypes.c_int32), ("fuse_mark", ctypes.c_int32), ("relax_blocks", ctypes.c_int32),
-                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("window33", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -127,11 +128,12 @@ def lib():
         L.bf_serve_close.restype = None
         L.bf_solve_noalloc.argtypes = [P, P, P, P, P, i64, P, P, P, P, P]
         L.bf_tune.argtypes = [P, P, P, P, P, P, P]
+        L.bf_set_schedule.argtypes = [P, P, P]
         L.bf_last_error.restype = ctypes.c_char_p
         for name in ("abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes",
                      "abs_export_boxes", "abs_export_pred", "abs_info",
                      "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
-                     "bf_solve_noalloc", "bf_tune"):
+                     "bf_solve_noalloc", "bf_tune", "bf_set_schedule"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -345,6 +347,13 @@ def bf_tune(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0,
     _check(lib().bf_tune(abstraction.handle, _ptr(Gc), _ptr(tg), _ptr(av), ctypes.byref(opts), ctypes.byref(res),
                          _stream(stream)))
     return {k: getattr(res, k) for k, _ in res._fields_}
+
+
+def bf_set_schedule(abstraction, slice_target=2, fuse_mark=1, relax_blocks=0, window33=0, stream=None):
+    """Put a pass schedule in force on this abstraction's solves (no timing)."""
+    s = TuneResult()
+    s.slice_target, s.fuse_mark, s.relax_blocks, s.window33 = slice_target, fuse_mark, relax_blocks, window33
+    _check(lib().bf_set_schedule(abstraction.handle, ctypes.byref(s), _stream(stream)))
 
 
 def bf_solve_batch(abstractions, Gs, targets=None, avoids=None, terminals=None, max_iters=0, Vs=None,

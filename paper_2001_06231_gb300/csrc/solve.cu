@@ -36,6 +36,8 @@ struct bf_solve_ws {
     long long* Vnew = nullptr;
     long long* M2 = nullptr;
     long long* M3 = nullptr;
+    long long* M33 = nullptr;       // D >= 2: 3 x 3 windows on dims 0-1 (not with a successor class)
+    bool use33 = false;             // gathers read M33 (bf_tune may switch it on)
     unsigned char* mu = nullptr;
     unsigned* fbits = nullptr;
     int* cells = nullptr;
@@ -80,7 +82,7 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     if (!w) return;
     if (w->exec) cudaGraphExecDestroy(w->exec);
     if (w->graph) cudaGraphDestroy(w->graph);
-    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->M2); cudaFree(w->M3); cudaFree(w->mu);
+    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->M2); cudaFree(w->M3); cudaFree(w->M33); cudaFree(w->mu);
     cudaFree(w->fbits); cudaFree(w->cells); cudaFree(w->chg); cudaFree(w->Gint); cudaFree(w->ctr);
     cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt); cudaFree(w->stage_avoid);
     cudaFree(w->stage_V); cudaFree(w->trace); cudaFree(w->stamp);
@@ -160,8 +162,10 @@ __global__ void k_init_values(long long C, const double* __restrict__ terminal,
 
 __global__ void k_init_tables(InstView v) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < v.g.C;
-         c += (long long)gridDim.x * blockDim.x)
+         c += (long long)gridDim.x * blockDim.x) {
         table_entry(v, c);
+        if (v.M33) table33_entry(v, c);
+    }
 }
 
 __global__ void k_init_counters(Counters* ctr, long long cap) {
@@ -272,6 +276,7 @@ static int ws_get(const bf_abstraction* a, bf_solve_ws** out) {
     A((void**)&w->Vnew, 8 * C);
     A((void**)&w->M2, 8 * C);
     A((void**)&w->M3, 8 * C);
+    if (w->D >= 2) A((void**)&w->M33, 8 * C);
     A((void**)&w->mu, C);
     A((void**)&w->fbits, 4 * S);
     A((void**)&w->cells, 4 * C);
@@ -293,6 +298,7 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.Vnew = w->Vnew;
     v.M2 = w->M2;
     v.M3 = w->M3;
+    v.M33 = (w->cls || !w->use33) ? nullptr : w->M33;   // the class tables have no 3 x 3 windows
     v.mu = w->mu;
     v.fbits = w->fbits;
     v.cells = w->cells;
@@ -395,6 +401,34 @@ static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
     w->compact_blocks = blocks_for(w->nwords, 256);
 }
 
+// Launch shapes and slice buffers (once per workspace; caller holds w->mtx).
+static int ws_blocks(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
+    if (w->relax_blocks) return BF_OK;
+    switch (a->g.D) {
+        case 1: set_blocks<1>(a, w); break;
+        case 2: set_blocks<2>(a, w); break;
+        case 3: set_blocks<3>(a, w); break;
+        default: set_blocks<4>(a, w); break;
+    }
+    // slice buffers: a sliced pass has nchunks < slice_target x warps and
+    // fewer than 2 x slice_target x warps (chunk, slice) items
+    w->relax_blocks_full = w->relax_blocks;
+    const long long warps = (long long)w->relax_blocks * 8;
+    const long long cap = 2LL * kSliceTargetMax * warps * 32;
+    cudaError_t e = cudaMalloc((void**)&w->cand_key, sizeof(long long) * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w->cand_u, sizeof(int) * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w->slice_cnt, sizeof(int) * (cap / 32));
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->slice_cnt, 0, sizeof(int) * (cap / 32), st);
+    if (e != cudaSuccess) {
+        cudaFree(w->cand_key); cudaFree(w->cand_u); cudaFree(w->slice_cnt);
+        w->cand_key = nullptr; w->cand_u = nullptr; w->slice_cnt = nullptr;
+        w->relax_blocks = 0;
+        return bfh::cuda_fail(e, "slice buffers");
+    }
+    w->slice_cap = cap;
+    return BF_OK;
+}
+
 // Build (once per workspace) the graph: [loop condition] -> WHILE { pass }.
 static int ws_graph(const bf_abstraction* a, bf_solve_ws* w) {
     if (w->exec) return BF_OK;
@@ -468,30 +502,7 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     std::lock_guard<std::mutex> lock(w->mtx);
     const long long C = w->C;
     const int U = w->U;
-    if (!w->relax_blocks) {
-        switch (a->g.D) {
-            case 1: set_blocks<1>(a, w); break;
-            case 2: set_blocks<2>(a, w); break;
-            case 3: set_blocks<3>(a, w); break;
-            default: set_blocks<4>(a, w); break;
-        }
-        // slice buffers: a sliced pass has nchunks < slice_target x warps and
-        // fewer than 2 x slice_target x warps (chunk, slice) items
-        w->relax_blocks_full = w->relax_blocks;
-        const long long warps = (long long)w->relax_blocks * 8;
-        const long long cap = 2LL * kSliceTargetMax * warps * 32;
-        cudaError_t e = cudaMalloc((void**)&w->cand_key, sizeof(long long) * cap);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&w->cand_u, sizeof(int) * cap);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&w->slice_cnt, sizeof(int) * (cap / 32));
-        if (e == cudaSuccess) e = cudaMemsetAsync(w->slice_cnt, 0, sizeof(int) * (cap / 32), st);
-        if (e != cudaSuccess) {
-            cudaFree(w->cand_key); cudaFree(w->cand_u); cudaFree(w->slice_cnt);
-            w->cand_key = nullptr; w->cand_u = nullptr; w->slice_cnt = nullptr;
-            w->relax_blocks = 0;
-            return bfh::cuda_fail(e, "slice buffers");
-        }
-        w->slice_cap = cap;
-    }
+    if ((rc = ws_blocks(a, w, st))) return rc;
     // schedule (the graph holds the view by value: rebuild it on a change)
     const int sched = opts ? opts->schedule : BF_SCHED_JACOBI;
     if (sched != BF_SCHED_JACOBI && sched != BF_SCHED_INPLACE) {
@@ -657,11 +668,12 @@ static int tune_time(const bf_abstraction* a, const double* G, const uint8_t* ta
     return rc;
 }
 
-static void set_schedule(bf_solve_ws* w, int slice_target, bool fuse, int blocks) {
+static void set_schedule(bf_solve_ws* w, int slice_target, bool fuse, int blocks, bool use33) {
     std::lock_guard<std::mutex> lock(w->mtx);
     w->slice_target = slice_target;
     w->fuse_mark = fuse;
     w->relax_blocks = blocks;
+    w->use33 = use33 && w->M33 != nullptr;
     w->tuned = true;
     if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
     if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
@@ -695,33 +707,60 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     if (rc) { cudaFree(V); cudaFree(mu); return rc; }
     const int full = w->relax_blocks_full;
     int b_slice = w->slice_target, b_blocks = w->relax_blocks;
-    bool b_fuse = w->fuse_mark;
+    bool b_fuse = w->fuse_mark, b_33 = w->use33;
     out->default_ms = best;
     int tried = 1;
     const int slices[4] = {0, 1, 2, kSliceTargetMax};
-    for (int si = 0; si < 4 && rc == BF_OK; ++si)
-        for (int f = 0; f < 2 && rc == BF_OK; ++f)
-            for (int bi = 0; bi < 2 && rc == BF_OK; ++bi) {
-                const int blocks = bi == 0 ? full : (full + 1) / 2;
-                set_schedule(w, slices[si], f != 0, blocks);
-                double ms = 0.0;
-                rc = tune_time(a, G, target, avoid, &o, V, mu, st, &ms);
-                ++tried;
-                if (rc == BF_OK && ms < best) {
-                    best = ms;
-                    b_slice = slices[si];
-                    b_fuse = f != 0;
-                    b_blocks = blocks;
+    const int n33 = (w->M33 && !(opts && opts->succ_class)) ? 2 : 1;
+    for (int t33 = 0; t33 < n33 && rc == BF_OK; ++t33)
+        for (int si = 0; si < 4 && rc == BF_OK; ++si)
+            for (int f = 0; f < 2 && rc == BF_OK; ++f)
+                for (int bi = 0; bi < 2 && rc == BF_OK; ++bi) {
+                    const int blocks = bi == 0 ? full : (full + 1) / 2;
+                    set_schedule(w, slices[si], f != 0, blocks, t33 != 0);
+                    double ms = 0.0;
+                    rc = tune_time(a, G, target, avoid, &o, V, mu, st, &ms);
+                    ++tried;
+                    if (rc == BF_OK && ms < best) {
+                        best = ms;
+                        b_slice = slices[si];
+                        b_fuse = f != 0;
+                        b_blocks = blocks;
+                        b_33 = t33 != 0;
+                    }
                 }
-            }
-    set_schedule(w, b_slice, b_fuse, b_blocks);
+    set_schedule(w, b_slice, b_fuse, b_blocks, b_33);
     cudaFree(V);
     cudaFree(mu);
     if (rc) return rc;
     out->slice_target = b_slice;
     out->fuse_mark = b_fuse ? 1 : 0;
+    out->window33 = b_33 ? 1 : 0;
     out->relax_blocks = b_blocks;
     out->candidates = tried;
     out->best_ms = best;
+    return BF_OK;
+}
+
+extern "C" int bf_set_schedule(const bf_abstraction* a, const bf_tune_result* sched, void* stream) {
+    if (!a || !sched) {
+        bfh::set_error("bf_set_schedule: NULL argument");
+        return BF_ERR_INVALID;
+    }
+    const int st_ = sched->slice_target;
+    if (st_ < 0 || st_ > kSliceTargetMax) {
+        bfh::set_error("bf_set_schedule: slice_target %d outside 0..%d", st_, kSliceTargetMax);
+        return BF_ERR_INVALID;
+    }
+    bf_solve_ws* w = nullptr;
+    int rc = ws_get(a, &w);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(w->mtx);
+        if ((rc = ws_blocks(a, w, (cudaStream_t)stream))) return rc;
+    }
+    int blocks = sched->relax_blocks;
+    if (blocks <= 0 || blocks > w->relax_blocks_full) blocks = w->relax_blocks_full;
+    set_schedule(w, st_, sched->fuse_mark != 0, blocks, sched->window33 != 0);
     return BF_OK;
 }

@@ -7,6 +7,8 @@
 //   M2, M3      int64 [C]  window maxima along dim 0: M2(y) = max(V(y), V(y+1)),
 //                          M3(y) = max(V(y..y+2)) (wrapping on a periodic dim 0),
 //                          equal to V's windows at the start of every pass
+//   M33         int64 [C]  (single solve) max of V over y0..y0+2 x y1..y1+2 on
+//                          dims 0-1 (wrapping on periodic dims), same refresh
 //   fbits       u32 [S]    upcoming frontier F2, one bit per cell
 //   cells       i32 [C]    current frontier F1 as a compacted cell list
 //   chg         i32 [C]    cells whose W decreased in the current pass
@@ -78,6 +80,7 @@ struct InstView {
     long long* Vnew;            // [C]
     long long* M2;              // [C]
     long long* M3;              // [C]
+    long long* M33;             // [C] max of V over 3 x 3 cells on dims 0-1, or NULL
     unsigned char* mu;          // [C]
     unsigned* fbits;            // [S]
     int* cells;                 // [C]
@@ -210,14 +213,19 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
             lo[d] = l;
         }
     }
-    // successor classes: V off the class in VN / M2 / M3, on it in VR / M2R / M3R
-    const long long* tab = w[0] == 1 ? (CLS ? v.VN : v.Vkey) : (w[0] == 2 ? v.M2 : v.M3);
+    // successor classes: V off the class in VN / M2 / M3, on it in VR / M2R / M3R.
+    // A box at least 3 cells wide on dims 0 and 1 reads 3 x 3 windows (M33):
+    // ceil(w0/3) x ceil(w1/3) lookups per dims >= 2 place instead of ceil(w0/3) x w1.
+    bool use33 = false;
+    if constexpr (!CLS && D >= 2) use33 = v.M33 != nullptr && w[0] >= 3 && w[1] >= 3;
+    const long long* tab = use33 ? v.M33 : (w[0] == 1 ? (CLS ? v.VN : v.Vkey) : (w[0] == 2 ? v.M2 : v.M3));
     const int np = w[0] < 3 ? 1 : (w[0] + 2) / 3;            // lookups per row
-    const int total = np * w[1] * w[2] * w[3];
-    // lookup e = q + np (j1 + w1 (j2 + w2 j3)); below 2^23 lookups (every box
+    const int n1 = use33 ? (w[1] + 2) / 3 : w[1];            // lookups along dim 1
+    const int total = np * n1 * w[2] * w[3];
+    // lookup e = q + np (j1 + n1 (j2 + w2 j3)); below 2^23 lookups (every box
     // of a real system) its digits come from multiply-high quotients
     const bool quick = (unsigned)total < kSmallDivMax;
-    const unsigned inv_q = kRecip.m[np], inv_1 = kRecip.m[w[1]], inv_2 = kRecip.m[w[2]];
+    const unsigned inv_q = kRecip.m[np], inv_1 = kRecip.m[n1], inv_2 = kRecip.m[w[2]];
     const long long* p = tab + (mine ? c + rel[0] : 0);
     long long m0 = kKeyMin, m1 = kKeyMin;
     const long long* pr = nullptr;
@@ -235,7 +243,7 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
                     j[1] = (int)t1;
                 } else if constexpr (D >= 3) {
                     const unsigned t2 = small_div(t1, inv_1);
-                    j[1] = (int)(t1 - t2 * w[1]);
+                    j[1] = (int)(t1 - t2 * n1);
                     if constexpr (D == 3) {
                         j[2] = (int)t2;
                     } else {
@@ -248,11 +256,12 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
                 int t = e;
                 q = t % np;
                 t /= np;
-                j[1] = t % w[1];
-                t /= w[1];
+                j[1] = t % n1;
+                t /= n1;
                 j[2] = t % w[2];
                 j[3] = t / w[2];
             }
+            if (use33) j[1] = min(3 * j[1], w[1] - 3);         // window rows j1 .. j1 + 2
             off = w[0] < 3 ? 0 : min(3 * q, w[0] - 3);
 #pragma unroll
             for (int d = 1; d < D; ++d) {
@@ -872,10 +881,47 @@ __device__ __forceinline__ void table_entry(const InstView& v, long long e) {
 
 // Refresh the entries whose window holds the changed cell y (e = y-2 .. y,
 // inside its row or wrapping on a periodic dim 0).
+// Recompute M33 at cell e from Vnew: the max over cells e0 .. e0 + 2 on dim
+// 0 and e1 .. e1 + 2 on dim 1 (wrapping on periodic dims; the part inside the
+// grid past a non-periodic edge, where no box reads it).
+// base: cell (0, 0) of the entry's dims-0/1 plane; x0, x1: its coordinates.
+__device__ __forceinline__ void table33_at(const InstView& v, long long base, int x0, int x1) {
+    const GridDesc& g = v.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    long long m = kKeyMin;
+    for (int b = 0; b < 3 && b < n1; ++b) {
+        int r = x1 + b;
+        if (r >= n1) {
+            if (!g.periodic[1]) break;
+            r -= n1;
+        }
+        const long long* row = v.Vnew + base + (long long)r * n0;
+        for (int a = 0; a < 3 && a < n0; ++a) {
+            int c = x0 + a;
+            if (c >= n0) {
+                if (!g.periodic[0]) break;
+                c -= n0;
+            }
+            m = max(m, row[c]);
+        }
+    }
+    v.M33[base + (long long)x1 * n0 + x0] = m;
+}
+
+__device__ __forceinline__ void table33_entry(const InstView& v, long long e) {
+    const GridDesc& g = v.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    const long long rowq = (long long)grid_div(g, 0, (unsigned)e);
+    const int x0 = (int)(e - rowq * n0);
+    const int x1 = (int)(rowq - (long long)grid_div(g, 1, (unsigned)rowq) * n1);
+    table33_at(v, e - x0 - (long long)x1 * n0, x0, x1);
+}
+
 __device__ __forceinline__ void refresh_tables(const InstView& v, long long y) {
     const GridDesc& g = v.g;
     const int n0 = g.n[0];
-    const long long row = (long long)grid_div(g, 0, (unsigned)y) * n0;
+    const long long rq = (long long)grid_div(g, 0, (unsigned)y);
+    const long long row = rq * n0;
     const int x = (int)(y - row);
     for (int j = 0; j < 3 && j < n0; ++j) {
         int xe = x - j;
@@ -884,6 +930,55 @@ __device__ __forceinline__ void refresh_tables(const InstView& v, long long y) {
             xe += n0;
         }
         table_entry(v, row + xe);
+    }
+    if (v.M33) {
+        // the 3 x 3 windows holding y start at (x - a, x1 - b), a, b in 0..2:
+        // read Vnew once over the 5 x 5 block around y (cells outside a
+        // non-periodic edge count as kKeyMin, periodic dims wrap), take the
+        // 3-cell row windows, then the 3-row column windows
+        const int n1 = g.n[1];
+        const int x1 = (int)(rq - (long long)grid_div(g, 1, (unsigned)rq) * n1);
+        const long long base = row - (long long)x1 * n0;
+        long long w3[5][3];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            int r = x1 - 2 + i;
+            bool rin = true;
+            if (r < 0) { if (g.periodic[1]) r += n1; else rin = false; }
+            else if (r >= n1) { if (g.periodic[1]) r -= n1; else rin = false; }
+            if (rin && (r < 0 || r >= n1)) r = ((r % n1) + n1) % n1;   // n1 < 3 on a periodic dim
+            long long cv[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                int c = x - 2 + k;
+                bool cin = rin;
+                if (c < 0) { if (g.periodic[0]) c += n0; else cin = false; }
+                else if (c >= n0) { if (g.periodic[0]) c -= n0; else cin = false; }
+                if (cin && (c < 0 || c >= n0)) c = ((c % n0) + n0) % n0;
+                cv[k] = cin ? v.Vnew[base + (long long)r * n0 + c] : kKeyMin;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) w3[i][a] = max(cv[2 - a], max(cv[3 - a], cv[4 - a]));
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            int r = x1 - b;
+            if (r < 0) {
+                if (!g.periodic[1]) break;
+                r += n1;
+                if (r < 0) break;                     // n1 < 3: the entry repeats
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int c = x - a;
+                if (c < 0) {
+                    if (!g.periodic[0]) break;
+                    c += n0;
+                    if (c < 0) break;
+                }
+                v.M33[base + (long long)r * n0 + c] = max(w3[2 - b][a], max(w3[3 - b][a], w3[4 - b][a]));
+            }
+        }
     }
 }
 
