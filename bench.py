@@ -258,7 +258,11 @@ def ours(args, rank, world, local_rank):
 
     # pass schedule picked by timing (slice target, marking, relax grid); results do not depend on it
     tuned = None
-    if not args.no_tune:
+    if args.set_schedule:
+        st_, fm_, rb_, w33_ = (int(x) for x in args.set_schedule.split(","))
+        bf.bf_set_schedule(A, slice_target=st_, fuse_mark=fm_, relax_blocks=rb_, window33=w33_, stream=stream)
+        tuned = {"slice_target": st_, "fuse_mark": fm_, "relax_blocks": rb_, "window33": w33_, "source": "--set-schedule"}
+    elif not args.no_tune:
         tuned = bf.bf_tune(A, G, target=tg, avoid=av, stream=stream)
     # canonical work (exact F1 of Algorithm 1 with Jacobi passes), counted once on the device
     rc = solve(count_exact=True, schedule=bf.SCHED_JACOBI)
@@ -676,6 +680,10 @@ def main():
                     help="build the abstraction in recompute mode (boxes regenerated inside relax)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default pass schedule (no bf_tune)")
+    ap.add_argument("--set-schedule", default=None, metavar="S,F,B,W",
+                    help="put this pass schedule in force instead of bf_tune: slice target, marking in relax (0/1), "
+                         "relax blocks (0: one wave), 3 x 3 window table (0/1) -- reproduces a tuned schedule "
+                         "under a profiler, whose timings would sway bf_tune")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the passes from the host instead of one graph launch per solve "
