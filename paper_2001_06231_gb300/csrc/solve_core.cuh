@@ -328,13 +328,12 @@ __device__ __forceinline__ bool box_has_stamp(const int* __restrict__ stamp, con
 // propagate
 // ---------------------------------------------------------------------------
 
-// Set the bits `mask` of word wd of the upcoming frontier; the word is read
-// first and updated with atomicOr only when some of its bits are still clear
-// (the predecessor boxes of neighbouring changed cells overlap, so most marks
-// end at the read).  Bits only go from 0 to 1 during propagate, so a stale
-// read can only cost a redundant atomic.
+// Set the bits `mask` of word wd of the upcoming frontier.  The atomicOr's
+// result is not used, so it is a reduction the warp does not wait for (no
+// read of the word first: the predecessor boxes of neighbouring changed cells
+// overlap, and a read that finds the bits set still costs an L2 round trip).
 __device__ __forceinline__ void mark_word(unsigned* fbits, int wd, unsigned mask) {
-    if ((fbits[wd] & mask) != mask) atomicOr(&fbits[wd], mask);
+    atomicOr(&fbits[wd], mask);
 }
 
 __device__ __forceinline__ unsigned bit_range(int s, int e) {
