@@ -148,6 +148,43 @@ def random_tiny(rng, nonneg=False):
     return n, periodic, boxes, G, T
 
 
+def test_pred_by_definition_tiny():
+    """pred(y) = {x : exists u, y in F(x,u)} (Eq. (pred)) written out: every
+    box of every pair enumerated cell by cell in Python (indexes wrapping on
+    periodic dims, up to the whole circle; blocked pairs have no successor),
+    against the oracle's CSR lists, which it also promises sorted by x."""
+    import itertools
+    rng = np.random.default_rng(2020)
+    shapes = [([5], [False]), ([6], [True]), ([4, 3], [False, True]), ([3, 4], [True, True]),
+              ([3, 4, 2], [True, False, True]), ([3, 2, 2, 3], [False, True, False, True])]
+    for n, per in shapes:
+        D, C, U = len(n), int(np.prod(n)), 3
+        strides = np.concatenate([[1], np.cumprod(n)[:-1]]).astype(int)
+        boxes = np.zeros((C, U, 2, D), dtype=np.int16)
+        for x in range(C):
+            for u in range(U):
+                if rng.random() < 0.1:
+                    boxes[x, u, 0, 0] = oracle.BLOCKED
+                    continue
+                for d in range(D):
+                    w = int(rng.integers(1, n[d] + 1))
+                    lo = int(rng.integers(0, n[d])) if per[d] else int(rng.integers(0, n[d] - w + 1))
+                    boxes[x, u, 0, d], boxes[x, u, 1, d] = lo, lo + w - 1
+        ptr, col = oracle.pred(n, per, boxes)
+        expect = [set() for _ in range(C)]
+        for x in range(C):
+            for u in range(U):
+                lo, hi = boxes[x, u, 0], boxes[x, u, 1]
+                if lo[0] == oracle.BLOCKED:
+                    continue
+                axes = [[k % n[d] for k in range(lo[d], hi[d] + 1)] for d in range(D)]
+                for y in itertools.product(*axes):
+                    expect[int(np.dot(y, strides))].add(x)
+        for y in range(C):
+            got = col[ptr[y]:ptr[y + 1]].tolist()
+            assert got == sorted(expect[y]), (n, per, y)
+
+
 def test_brute_force_random_tiny():
     rng = np.random.default_rng(7)
     checked = 0
