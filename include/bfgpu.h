@@ -262,12 +262,12 @@ BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *t
  * whether relax marks the next frontier itself or a propagate launch does,
  * the relax grid (one or half a wave) and, on grids of 2 or more dims,
  * whether boxes at least 3 cells wide on dims 0 and 1 read a table of 3 x 3
- * window maxima (fewer gathers, more table upkeep per changed cell).  Each of
- * the 16 (32) candidates is
- * solved three times on the given inputs (G, target, avoid and the optional
- * terminal / succ_class / G_class / max_iters of opts; flags, trace and stats
- * are ignored); the fastest stays in force for later bf_solve calls on the
- * handle.  Results never depend on the schedule.  Errors: as bf_solve. */
+ * window maxima (fewer gathers, more table upkeep per changed cell; not
+ * with a successor class).  Each of the 16 candidates (32 with the window
+ * table) is solved three times on the given inputs (G, target, avoid and the
+ * optional terminal / succ_class / G_class / max_iters of opts; flags, trace
+ * and stats are ignored); the fastest stays in force for later bf_solve calls
+ * on the handle.  Results never depend on the schedule.  Errors: as bf_solve. */
 typedef struct {
     int32_t slice_target;
     int32_t fuse_mark;         /* 1: relax marks the next frontier                */
