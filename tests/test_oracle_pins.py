@@ -504,6 +504,27 @@ def test_builder_double_integrator_sound_and_tight():
     assert nblocked > 0
 
 
+def test_builder_half_open_cells_exact_edges():
+    """Quantisation on exact cell edges (half-open cells: a face on an edge
+    takes the upper cell; a box past a non-periodic edge is blocked).  Unit
+    cells, tau = 1: the double integrator maps cell [k0, k0+1] x [k1, k1+1]
+    under u to x0 + x1 + u/2 in [k0+k1+u/2, k0+k1+2+u/2] and x1 + u in
+    [k1+u, k1+1+u], every corner image an integer, so the box is
+    [k0+k1+u/2, k0+k1+2+u/2] x [k1+u, k1+1+u], blocked once it leaves 0..7."""
+    n = (8, 8)
+    inputs = np.array([[0.0], [2.0], [-2.0]])
+    boxes = oracle.build_boxes(oracle.LINEAR2D, (), 1, n, (0.0, 0.0), (8.0, 8.0), (False, False), inputs, 1.0)
+    for c in range(64):
+        k0, k1 = c % 8, c // 8
+        for ui, u in enumerate(inputs[:, 0]):
+            lo = (k0 + k1 + int(u) // 2, k1 + int(u))
+            hi = (k0 + k1 + 2 + int(u) // 2, k1 + 1 + int(u))
+            if min(lo) < 0 or max(hi) > 7:
+                assert boxes[c, ui, 0, 0] == oracle.BLOCKED, (c, u)
+            else:
+                assert tuple(boxes[c, ui, 0]) == lo and tuple(boxes[c, ui, 1]) == hi, (c, u, boxes[c, ui])
+
+
 def test_builder_unicycle_centre_closed_form():
     rng = np.random.default_rng(9)
     for _ in range(40):
