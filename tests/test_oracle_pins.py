@@ -525,6 +525,30 @@ def test_builder_half_open_cells_exact_edges():
                 assert tuple(boxes[c, ui, 0]) == lo and tuple(boxes[c, ui, 1]) == hi, (c, u, boxes[c, ui])
 
 
+@pytest.mark.parametrize("n0", [8, 3])
+def test_builder_periodic_wrap_exact_edges(n0):
+    """The same unit-cell double integrator with dim 0 periodic: the 3-cell
+    range on dim 0 wraps (lower cell taken mod n0, upper = lower + 2, the
+    indexes past n0 - 1 wrapping) and is the whole circle (0 .. n0 - 1) once
+    3 >= n0; dim 1 still blocks past its edges."""
+    n = (n0, 8)
+    inputs = np.array([[0.0], [2.0], [-2.0]])
+    boxes = oracle.build_boxes(oracle.LINEAR2D, (), 1, n, (0.0, 0.0), (float(n0), 8.0), (True, False), inputs, 1.0)
+    for c in range(n0 * 8):
+        k0, k1 = c % n0, c // n0
+        for ui, u in enumerate(inputs[:, 0]):
+            lo1, hi1 = k1 + int(u), k1 + 1 + int(u)
+            if lo1 < 0 or hi1 > 7:
+                assert boxes[c, ui, 0, 0] == oracle.BLOCKED, (c, u)
+                continue
+            if n0 <= 3:
+                lo0, hi0 = 0, n0 - 1
+            else:
+                lo0 = (k0 + k1 + int(u) // 2) % n0
+                hi0 = lo0 + 2
+            assert tuple(boxes[c, ui, 0]) == (lo0, lo1) and tuple(boxes[c, ui, 1]) == (hi0, hi1), (c, u)
+
+
 def test_builder_unicycle_centre_closed_form():
     rng = np.random.default_rng(9)
     for _ in range(40):
