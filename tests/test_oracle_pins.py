@@ -203,6 +203,43 @@ def test_brute_force_random_tiny():
     assert checked >= 30
 
 
+def test_brute_force_tiny_3d_4d():
+    """The brute force over static controllers on 3- and 4-D grids of 8 cells
+    (dims of size 1 included, periodic or not): the oracle's cell indexing,
+    box walk and predecessor lists in more than two dims."""
+    rng = np.random.default_rng(34)
+    shapes = [(2, 2, 2), (3, 1, 2), (2, 1, 2, 2), (1, 2, 2, 2), (2, 2, 1, 2)]
+    checked = 0
+    for trial in range(40):
+        n = list(shapes[trial % len(shapes)])
+        D, C, U = len(n), int(np.prod(n)), 2
+        periodic = [bool(rng.integers(0, 2)) for _ in range(D)]
+        boxes = np.zeros((C, U, 2, D), dtype=np.int16)
+        for x in range(C):
+            for u in range(U):
+                if rng.random() < 0.1:
+                    boxes[x, u, 0, 0] = oracle.BLOCKED
+                    continue
+                for d in range(D):
+                    lo = int(rng.integers(0, n[d]))
+                    hi = lo + min(int(rng.integers(0, 2)), n[d] - 1)     # at most the whole circle
+                    if not periodic[d]:
+                        hi = min(hi, n[d] - 1)
+                    boxes[x, u, 0, d], boxes[x, u, 1, d] = lo, hi
+        G = rng.integers(-1 if trial % 2 else 0, 5, size=(C, U)).astype(np.float64)
+        T = rng.integers(0, 5, size=C).astype(np.float64)
+        T[rng.random(C) < 0.5] = INF
+        r = oracle.solve(n, periodic, boxes, G, T)
+        if r["status"] != oracle.CONVERGED:
+            continue
+        F = brute.boxes_to_successors(n, periodic, boxes)
+        gfun = lambda x, y, u: float(G[x, u])
+        assert brute.brute_force_value(F, T.tolist(), gfun) == r["V"].tolist(), trial
+        assert brute.performance(F, T.tolist(), gfun, brute.controller_sets(r["mu"], U)) == r["V"].tolist(), trial
+        checked += 1
+    assert checked >= 20
+
+
 def test_successor_class_cost_brute_force():
     """Running cost that depends on the successor (Sec. VI-A, g2: a reward for
     successors in a set, another cost elsewhere), g(x,y,u) = Gc(x,u) for y in
