@@ -353,6 +353,33 @@ def test_dijkstra_equals_bellman_ford_random():
         assert np.array_equal(r["V"], Vd), trial
 
 
+@pytest.mark.parametrize("n", [[9, 7, 6], [6, 5, 4, 4]])
+def test_dijkstra_equals_bellman_ford_3d_4d(n):
+    """Min-max Dijkstra and Algorithm 1 agree bit for bit on random 3- and
+    4-D abstractions with non-negative costs."""
+    rng = np.random.default_rng(len(n) * 17)
+    D, C = len(n), int(np.prod(n))
+    coords = np.stack(np.unravel_index(np.arange(C), tuple(reversed(n)))[::-1], axis=1)
+    for trial in range(4):
+        U = int(rng.integers(4, 7))
+        # mostly one-cell boxes (a worst case over many cells rarely stays finite in 3-4 D)
+        lo = coords[:, None, :] + rng.integers(-1, 2, size=(C, U, D))
+        hi = lo + (rng.random((C, U, D)) < 0.1)
+        ok = np.all((lo >= 0) & (hi < np.array(n)), axis=2)
+        boxes = np.stack([lo, hi], axis=2).astype(np.int16)
+        boxes[~ok, 0, 0] = oracle.BLOCKED
+        G = rng.integers(0, 8, size=(C, U)) * 0.125
+        T = np.full(C, INF)
+        T[rng.choice(C, size=12, replace=False)] = rng.integers(0, 4, size=12) * 0.5
+        avoid = (rng.random(C) < 0.05).astype(np.uint8)
+        per = [False] * len(n)
+        r = oracle.solve(n, per, boxes, G, T, avoid)
+        assert r["status"] == oracle.CONVERGED
+        Vd, _ = oracle.dijkstra(n, per, boxes, G, T, avoid)
+        assert np.array_equal(r["V"], Vd), trial
+        assert np.isfinite(r["V"]).sum() > C // 2              # the values spread past the targets
+
+
 @pytest.mark.parametrize("tau", [0.1, 0.3])
 def test_dijkstra_equals_bellman_ford_double_integrator(tau):
     w = wl.di2d(tau=tau)
