@@ -3,15 +3,19 @@
 
 Metric: (cell, input) relaxations per second of Algorithm 1 solving to its
 fixed point.  One step = one bf_solve call (set-up of lines 1-10, every pass
-of the while-loop, output) on the 3-D unicycle workload (200 x 200 x 64 cells
-x 10 inputs, stored boxes) with the abstraction already resident (its build
-is timed separately).  The numerator is the canonical work of Algorithm 1:
-the sum over passes of |F1| x |U| with the exact predecessor sets of Eq.
-(pred), counted once on the device in counting mode (deterministic: passes
-are synchronous).
+of the while-loop, output) with the abstraction already resident (its build is
+timed separately).  The default workload is the 4-D firefighting aircraft
+model on 100 x 100 x 36 x 8 cells x 15 inputs with stored boxes, at tau = 2 s
+and a wider landing box (at tau = 1 s with the narrow landing box the instance
+is degenerate: a 10 m cell moves about one cell per step and the solve stops
+after 4 passes; that configuration is measured too and reported under
+"as_stated").  The numerator is the canonical work of Algorithm 1: the sum
+over passes of |F1| x |U| with the exact predecessor sets of Eq. (pred),
+counted once on the device in counting mode (deterministic: passes are
+synchronous).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload unicycle3d|fire4d|di2d]
+                    [--workload fire4d|unicycle3d|di2d|batched|served|mission]
 
 --impl reference times the CPU oracle (plain single-threaded FP64 C) on a
 bounded sample of the same workload (the first passes of the same solve).
@@ -34,9 +38,11 @@ import numpy as np  # noqa: E402
 
 METRIC = "(cell,input) relaxations/s"
 UNIT = "relaxations/s"
-PROFILE = os.path.join(ROOT, "profiles", "k_relax_unicycle3d_200x200x64.txt")
+PROFILES = {"unicycle3d": os.path.join(ROOT, "profiles", "k_relax_unicycle3d_200x200x64.txt"),
+            "fire4d": os.path.join(ROOT, "profiles", "k_relax_fire4d_100x100x36x8.txt")}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2001_06231_gb300", "csrc", f)
                   for f in ("solve_core.cuh", "solve.cu", "bf_internal.cuh", "dynamics.cuh")]
+FIRE_TARGET_WIDE = ((50.0, 250.0), (50.0, 150.0), (-0.5235987755982988, 0.5235987755982988), (10.0, 15.0))
 
 
 def kernel_hash():
@@ -54,9 +60,14 @@ def make_workload(name, rank=0):
         w = wl.unicycle3d(seed=wl.SEED_BASE + 2 + 1000 * rank)
         desc = "unicycle3d 200x200x64 cells x 10 inputs, tau 0.3 s, RK4 8 substeps, 40 obstacles, stored boxes"
     elif name == "fire4d":
-        w = wl.fire4d(seed=wl.SEED_BASE + 3 + 1000 * rank, tau=2.0,
-                      target=((50.0, 250.0), (50.0, 150.0), (-math.radians(30), math.radians(30)), (10.0, 15.0)))
-        desc = "fire4d 100x100x36x8 cells x 15 inputs, tau 2 s, negative costs over fire, stored boxes"
+        w = wl.fire4d(seed=wl.SEED_BASE + 3 + 1000 * rank, tau=2.0, target=FIRE_TARGET_WIDE)
+        desc = ("fire4d 100x100x36x8 cells x 15 inputs, tau 2 s, landing box [50,250]x[50,150] m x [-30,30] deg "
+                "x [10,15] m/s (the 4-D configuration at tau 2 s: at the stated tau 1 s it stops after 4 passes, "
+                "see as_stated), 5 fire blobs (negative costs), 6 no-fly boxes, stored boxes")
+    elif name == "fire4d_tau1":
+        w = wl.fire4d(seed=wl.SEED_BASE + 3 + 1000 * rank)
+        desc = ("fire4d 100x100x36x8 cells x 15 inputs as stated: tau 1 s, landing box [50,250]x[50,100] m x "
+                "[-10,10] deg x [10,12.5] m/s, 5 fire blobs, 6 no-fly boxes, stored boxes")
     elif name == "di2d":
         w = wl.di2d()
         desc = "di2d 64x64 cells x 5 inputs, tau 0.1 s, exact linear flow"
@@ -66,8 +77,14 @@ def make_workload(name, rank=0):
 
 
 def algorithmic_bytes_per_pair(A):
-    """HBM bytes one relaxation must stream: its box record + its cost (8 B)."""
+    """HBM bytes one executed relaxation streams here: its box record + its cost (8 B)."""
     return A.box_record_bytes + 8
+
+
+def canonical_bytes_per_pair(D):
+    """Algorithmic HBM bytes of one canonical relaxation: the stored box as D
+    int16 lower and D int16 upper corners (4 D bytes) plus the FP64 cost G."""
+    return 4 * D + 8
 
 
 def whole_job(units, seconds, dist=None, device=None):
@@ -318,24 +335,56 @@ def ours(args, rank, world, local_rank):
     h2d = w.G.nbytes + w.target.nbytes + w.avoid.nbytes
     d2h = 8 * C + C
 
-    # roofline of the relax kernel (dominant): algorithmic bytes per launch
+    # roofline of the relax kernel (dominant): algorithmic bytes per launch =
+    # canonical pairs per launch x (4 D B box + 8 B cost), over the mean CUDA-event
+    # time of a relax launch; the bytes the executed pairs stream here beside it
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    bpp = algorithmic_bytes_per_pair(A)
-    bytes_per_launch = executed * bpp / max(1, passes)
+    cbpp = canonical_bytes_per_pair(w.grid.ndim)
+    bytes_per_launch = canonical * cbpp / max(1, passes)
     achieved = bytes_per_launch / (relax_ms_avg / 1e3) / 1e9
+    bpp = algorithmic_bytes_per_pair(A)
+    exec_bytes_per_launch = executed * bpp / max(1, passes)
     traffic = None
-    if os.path.exists(PROFILE) and args.workload == "unicycle3d" and A.mode == bf.MODE_STORED:
-        kv = dict(l.split(":", 1) for l in open(PROFILE) if ":" in l and not l.startswith("#"))
+    prof = PROFILES.get(args.workload)
+    if prof and os.path.exists(prof) and A.mode == bf.MODE_STORED:
+        kv = dict(l.split(":", 1) for l in open(prof) if ":" in l and not l.startswith("#"))
         if kv.get("kernel_hash", "").strip() == kernel_hash():
             try:
                 traffic = float(kv["traffic_bytes_per_launch"])
             except (KeyError, ValueError):
                 traffic = None
+
+    # the 4-D configuration as stated (tau 1 s, narrow landing box): a few passes
+    as_stated = None
+    if args.workload == "fire4d" and not args.no_as_stated:
+        ws_, desc_s = make_workload("fire4d_tau1", rank)
+        A1 = bf.abs_build_workload(ws_)
+        G1 = torch.from_numpy(ws_.G).to(dev)
+        tg1 = torch.from_numpy(ws_.target).to(dev)
+        av1 = torch.from_numpy(ws_.avoid).to(dev)
+        if not args.no_tune and not args.set_schedule:
+            bf.bf_tune(A1, G1, target=tg1, avoid=av1, stream=stream)
+        c1 = bf.bf_solve(A1, G1, target=tg1, avoid=av1, V=V, mu=mu, stream=stream, count_exact=True)
+        can1 = c1["stats"]["exact_f1_cells"] * ws_.ninputs
+        for _ in range(args.warmup):
+            bf.bf_solve(A1, G1, target=tg1, avoid=av1, V=V, mu=mu, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            r1 = bf.bf_solve(A1, G1, target=tg1, avoid=av1, V=V, mu=mu, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1) / args.steps
+        as_stated = {"workload": desc_s, "value": can1 / (ms1 / 1e3), "unit": UNIT, "ms_per_step": ms1,
+                     "passes": r1["iters"], "status": r1["status"], "canonical_relaxations_per_step": can1,
+                     "executed_relaxations_per_step": c1["stats"]["executed_pairs"],
+                     "finite_cells": int(torch.isfinite(V).sum().item())}
+        del A1
 
     cpu = None
     builder_mismatch = None
@@ -365,10 +414,15 @@ def ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_relax",
                      "peak_source": peak_src, "relax_ms_per_launch": relax_ms_avg,
-                     "propagate_ms_per_launch": prop_ms_avg,
+                     "rest_of_pass_ms_per_launch": prop_ms_avg,
                      "bytes_per_launch": bytes_per_launch,
-                     "bytes_note": "executed (cell,input) pairs per launch x %d B (box record %d B + G 8 B)" % (
+                     "bytes_note": "canonical (cell,input) pairs per launch x %d B (%d int16 box corners + FP64 G)" % (
+                         cbpp, 2 * w.grid.ndim),
+                     "executed_bytes_per_launch": exec_bytes_per_launch,
+                     "executed_frac": exec_bytes_per_launch / (relax_ms_avg / 1e3) / 1e9 / peak,
+                     "executed_bytes_note": "executed pairs per launch x %d B (box record %d B + G 8 B)" % (
                          bpp, bpp - 8)},
+        "as_stated": as_stated,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
@@ -559,7 +613,10 @@ def served(args):
         return len(times) / span, lat
 
     # correctness spot check: a few served results equal solo solves
+    sampler = ClockSampler(0)
+    sampler.start()
     qps_s, lat_s, res_s, modes = run_served(arrivals)
+    clocks_offered = sampler.stop()
     for i in range(min(6, len(res_s))):
         k, w, _ = payloads[i % len(payloads)]
         ref = bf.bf_solve(resident[k], w.G, target=w.target, avoid=w.avoid)
@@ -567,9 +624,13 @@ def served(args):
             raise SystemExit("served request %d failed with error %d (budget %.2f GB too small for its system?)"
                              % (i, res_s[i]["error"], args.budget_gb))
         assert ref["iters"] == res_s[i]["iters"] and ref["status"] == res_s[i]["status"], i
+        assert np.array_equal(ref["V"], res_s[i]["V"]) and np.array_equal(ref["mu"], res_s[i]["mu"]), i
     qps_p, lat_p = run_plain(arrivals)
     sat = np.zeros(args.requests)
+    sampler = ClockSampler(0)
+    sampler.start()
     qps_s_sat, lat_s_sat, _, _ = run_served(sat)
+    clocks_sat = sampler.stop()
     qps_p_sat, lat_p_sat = run_plain(sat)
     pct = lambda a, q: float(np.percentile(a, q)) * 1e3
     line = {"metric": "queries/s", "value": qps_s, "unit": "queries/s", "n_gpus": 1, "steps": args.requests,
@@ -586,7 +647,8 @@ def served(args):
                        "saturated_p99_ms": pct(lat_s_sat, 99)},
             "plain_one_at_a_time": {"qps": qps_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
                                     "saturated_qps": qps_p_sat, "saturated_p50_ms": pct(lat_p_sat, 50),
-                                    "saturated_p99_ms": pct(lat_p_sat, 99)}}
+                                    "saturated_p99_ms": pct(lat_p_sat, 99)},
+            "clocks": clocks_offered, "clocks_saturated": clocks_sat}
     print(json.dumps(line), flush=True)
 
 
@@ -662,7 +724,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="unicycle3d",
+    ap.add_argument("--workload", default="fire4d",
                     choices=["unicycle3d", "fire4d", "di2d", "batched", "served", "mission"])
     ap.add_argument("--mission-cap", type=int, default=5000, help="mission: pass cap of each stage")
     ap.add_argument("--requests", type=int, default=600, help="served: number of requests")
@@ -685,6 +747,8 @@ def main():
                          "relax blocks (0: one wave), 3 x 3 window table (0/1) -- reproduces a tuned schedule "
                          "under a profiler, whose timings would sway bf_tune")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-as-stated", action="store_true",
+                    help="fire4d: skip the tau 1 s configuration as stated")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the passes from the host instead of one graph launch per solve "
                          "(profilers see every pass kernel)")

@@ -382,9 +382,10 @@ BF_API const char *bf_last_error(void);
  * state (values, frontier bitmap and lists, the transposed cost array,
  * counters) lives in one file-scope device array of BF_NOALLOC_SCRATCH_BYTES
  * bytes that every GPU which loads the library holds until the process
- * exits.  An instance needing more than that (about 20 + 8*U bytes per cell
- * plus small lists) is rejected with BF_ERR_INVALID and a message giving the
- * size it would need.
+ * exits.  An instance needing more than that (about 40 + 8*U bytes per cell:
+ * four int64 value and window arrays, two int32 cell lists, the frontier
+ * bitmap and the transposed FP64 costs) is rejected with BF_ERR_INVALID and a
+ * message giving the size it would need.
  *
  * Every array argument must be device memory of the current device (host
  * pointers are rejected with BF_ERR_INVALID, since copying them would need a
@@ -394,11 +395,15 @@ BF_API const char *bf_last_error(void);
  * Results are identical to bf_solve.
  *
  * The first call on a device looks up the device address of the scratch
- * array (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  All calls share the one array and it keeps the last
- * call's contents (each call clears what must start at zero), so calls that
- * may overlap on the GPU -- on different streams, or from different host
- * threads -- race and must be serialized by the caller. */
+ * array (cudaGetSymbolAddress) and caches it for the life of the process;
+ * make that first call before any stream capture, and do not call it on a
+ * device after cudaDeviceReset there (the cached address would be stale).
+ * The call drives the passes from the host: it reads the pass counters back
+ * and synchronizes the stream before it returns.  All calls share the one
+ * array and it keeps the last call's contents (each call clears what must
+ * start at zero), so calls that may overlap on the GPU -- on different
+ * streams, or from different host threads -- race and must be serialized by
+ * the caller. */
 #define BF_NOALLOC_SCRATCH_BYTES (32u << 20)
 BF_API int bf_solve_noalloc(const bf_abstraction *abs, const double *G, const uint8_t *target,
                             const uint8_t *avoid, const double *terminal, int64_t max_iters,

@@ -13,8 +13,6 @@
 #include <cstring>
 #include <mutex>
 
-#include <math_constants.h>
-
 #include "solve_core.cuh"
 
 using namespace bfk;
@@ -73,14 +71,6 @@ Layout plan(long long C, int U) {
     return L;
 }
 
-__device__ __forceinline__ bool clean_cost(double v, double& out) {
-    if (v != v) return false;
-    if (v == -CUDART_INF) return false;
-    if (v != CUDART_INF && fabs(v) > 18446744073709551616.0) return false;
-    out = (v == 0.0) ? 0.0 : v;
-    return true;
-}
-
 __global__ void k_na_counters(Counters* ctr, long long cap) {
     memset(ctr, 0, sizeof(Counters));
     ctr->cap = cap;
@@ -88,47 +78,13 @@ __global__ void k_na_counters(Counters* ctr, long long cap) {
 
 __global__ void k_na_costs(long long C, int U, const double* __restrict__ G,
                            const unsigned char* __restrict__ avoid, double* Gint, Counters* ctr) {
-    bool bad = false;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
-         c += (long long)gridDim.x * blockDim.x) {
-        const bool av = avoid && avoid[c];
-        for (int u = 0; u < U; ++u) {
-            double v;
-            if (!clean_cost(__ldg(G + c * U + u), v)) bad = true;
-            Gint[(long long)u * C + c] = av ? CUDART_INF : v;
-        }
-    }
-    if (bad) atomicOr(&ctr->err, 1);
+    init_costs_body(C, U, G, avoid, Gint, ctr);
 }
 
 __global__ void k_na_values(long long C, const double* __restrict__ terminal,
                             const unsigned char* __restrict__ target, const unsigned char* __restrict__ avoid,
                             long long* Vkey, long long* Vnew, unsigned char* mu, int* chg, Counters* ctr) {
-    bool bad = false;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long rounds = (C + stride - 1) / stride;
-    for (long long it = 0; it < rounds; ++it) {
-        const long long c = start + it * stride;
-        bool finite = false;
-        if (c < C) {
-            double t;
-            if (terminal) {
-                if (!clean_cost(terminal[c], t)) { bad = true; t = CUDART_INF; }
-            } else {
-                t = (target && target[c]) ? 0.0 : CUDART_INF;
-            }
-            if (avoid && avoid[c]) t = CUDART_INF;
-            const long long k = key_of(t);
-            Vkey[c] = k;
-            Vnew[c] = k;
-            mu[c] = kHandover;
-            finite = k != kKeyInf;
-        }
-        const int slot = warp_append(finite, &ctr->nchg);
-        if (finite) chg[slot] = (int)c;
-    }
-    if (bad) atomicOr(&ctr->err, 1);
+    init_values_body(C, terminal, target, avoid, Vkey, Vnew, mu, chg, nullptr, ctr);
 }
 
 __global__ void k_na_tables(InstView v) {
@@ -251,14 +207,16 @@ int run(const bf_abstraction* a, const InstView& v, const double* G, const unsig
     return BF_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory of device dev, or NULL.
+bool on_device(const void* p, int dev) {
     if (!p) return true;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -270,8 +228,10 @@ extern "C" int bf_solve_noalloc(const bf_abstraction* a, const double* G, const 
         bfh::set_error("bf_solve_noalloc: NULL argument (need G, V, mu, iters, status and target or terminal)");
         return BF_ERR_INVALID;
     }
-    if (!on_device(G) || !on_device(target) || !on_device(avoid) || !on_device(terminal) ||
-        !on_device(V) || !on_device(mu)) {
+    int dev = 0;
+    BF_CUDA(cudaGetDevice(&dev));
+    if (!on_device(G, dev) || !on_device(target, dev) || !on_device(avoid, dev) || !on_device(terminal, dev) ||
+        !on_device(V, dev) || !on_device(mu, dev)) {
         bfh::set_error("bf_solve_noalloc: every array must be device memory of the current device "
                        "(it does not stage host arrays)");
         return BF_ERR_INVALID;

@@ -96,68 +96,18 @@ void bf_solve_ws_free(bf_solve_ws* w) {
 // set-up kernels
 // ---------------------------------------------------------------------------
 
-// -0 -> +0; NaN, -inf and |finite| > 2^64 are errors.
-__device__ __forceinline__ bool clean_cost(double v, double& out) {
-    if (v != v) return false;
-    if (v == -CUDART_INF) return false;
-    if (v != CUDART_INF && fabs(v) > 18446744073709551616.0) return false;
-    out = (v == 0.0) ? 0.0 : v;
-    return true;
-}
-
-// Gint[u][c] = clean(G[c][u]), +inf on avoid cells.  Lanes take consecutive
-// cells of one input: the writes are coalesced and the strided reads of a
-// warp's 32 x U block are served from L1 across the u loop.
+// Set-up kernels (bodies in solve_core.cuh, shared with bf_solve_noalloc).
 __global__ void k_init_costs(long long C, int U, const double* __restrict__ G,
                              const unsigned char* __restrict__ avoid, double* Gint, Counters* ctr) {
-    bool bad = false;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
-         c += (long long)gridDim.x * blockDim.x) {
-        const bool av = avoid && avoid[c];
-        for (int u = 0; u < U; ++u) {
-            double v;
-            if (!clean_cost(__ldg(G + c * U + u), v)) bad = true;
-            Gint[(long long)u * C + c] = av ? CUDART_INF : v;
-        }
-    }
-    if (bad) atomicOr(&ctr->err, 1);
+    init_costs_body(C, U, G, avoid, Gint, ctr);
 }
 
-// Lines 1-9 of Algorithm 1: W = terminal cost (0 on target, +inf elsewhere,
-// or the caller's array), mu = U (hand over); the cells with finite W go to
-// the changed list so that the first propagate builds F1 from their preds.
 __global__ void k_init_values(long long C, const double* __restrict__ terminal,
                               const unsigned char* __restrict__ target,
                               const unsigned char* __restrict__ avoid, long long* Vkey,
                               long long* Vnew, unsigned char* mu, int* chg, int* stamp,
                               Counters* ctr) {
-    bool bad = false;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    // uniform trip count per warp so the ballot in warp_append is safe
-    const long long rounds = (C + stride - 1) / stride;
-    for (long long it = 0; it < rounds; ++it) {
-        const long long c = start + it * stride;
-        bool finite = false;
-        if (c < C) {
-            double t;
-            if (terminal) {
-                if (!clean_cost(terminal[c], t)) { bad = true; t = CUDART_INF; }
-            } else {
-                t = (target && target[c]) ? 0.0 : CUDART_INF;
-            }
-            if (avoid && avoid[c]) t = CUDART_INF;
-            const long long k = key_of(t);
-            Vkey[c] = k;
-            Vnew[c] = k;
-            mu[c] = kHandover;
-            finite = k != kKeyInf;
-            if (stamp) stamp[c] = finite ? -1 : -2;   // -1: "changed" before pass 0
-        }
-        const int slot = warp_append(finite, &ctr->nchg);
-        if (finite) chg[slot] = (int)c;
-    }
-    if (bad) atomicOr(&ctr->err, 1);
+    init_values_body(C, terminal, target, avoid, Vkey, Vnew, mu, chg, stamp, ctr);
 }
 
 __global__ void k_init_tables(InstView v) {

@@ -136,6 +136,78 @@ inline void view_from_abs(InstView& v, const bf_abstraction* a) {
 }
 
 // ---------------------------------------------------------------------------
+// set-up (lines 1-9 of Algorithm 1), shared by every solve entry point
+// ---------------------------------------------------------------------------
+
+// -0 -> +0; NaN, -inf and |finite| > 2^64 are errors.
+__device__ __forceinline__ bool clean_cost(double v, double& out) {
+    if (v != v) return false;
+    if (v == -__longlong_as_double(0x7FF0000000000000LL)) return false;
+    if (v != __longlong_as_double(0x7FF0000000000000LL) && fabs(v) > 18446744073709551616.0) return false;
+    out = (v == 0.0) ? 0.0 : v;
+    return true;
+}
+
+// Gint[u][c] = clean(G[c][u]), +inf on avoid cells (grid-stride over cells).
+// Lanes take consecutive cells of one input: the writes are coalesced and the
+// strided reads of a warp's 32 x U block are served from L1 across the u loop.
+__device__ __forceinline__ void init_costs_body(long long C, int U, const double* __restrict__ G,
+                                                const unsigned char* __restrict__ avoid, double* Gint,
+                                                Counters* ctr) {
+    const double inf = __longlong_as_double(0x7FF0000000000000LL);
+    bool bad = false;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x) {
+        const bool av = avoid && avoid[c];
+        for (int u = 0; u < U; ++u) {
+            double v;
+            if (!clean_cost(__ldg(G + c * U + u), v)) bad = true;
+            Gint[(long long)u * C + c] = av ? inf : v;
+        }
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+// Lines 1-9 of Algorithm 1: W = terminal cost (0 on target, +inf elsewhere,
+// or the caller's array), mu = U (hand over); the cells with finite W go to
+// the changed list so that the first propagate builds F1 from their preds.
+// stamp (counting mode) or NULL.
+__device__ __forceinline__ void init_values_body(long long C, const double* __restrict__ terminal,
+                                                 const unsigned char* __restrict__ target,
+                                                 const unsigned char* __restrict__ avoid, long long* Vkey,
+                                                 long long* Vnew, unsigned char* mu, int* chg, int* stamp,
+                                                 Counters* ctr) {
+    const double inf = __longlong_as_double(0x7FF0000000000000LL);
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // uniform trip count per warp so the ballot in warp_append is safe
+    const long long rounds = (C + stride - 1) / stride;
+    for (long long it = 0; it < rounds; ++it) {
+        const long long c = start + it * stride;
+        bool finite = false;
+        if (c < C) {
+            double t;
+            if (terminal) {
+                if (!clean_cost(terminal[c], t)) { bad = true; t = inf; }
+            } else {
+                t = (target && target[c]) ? 0.0 : inf;
+            }
+            if (avoid && avoid[c]) t = inf;
+            const long long k = key_of(t);
+            Vkey[c] = k;
+            Vnew[c] = k;
+            mu[c] = kHandover;
+            finite = k != kKeyInf;
+            if (stamp) stamp[c] = finite ? -1 : -2;   // -1: "changed" before pass 0
+        }
+        const int slot = warp_append(finite, &ctr->nchg);
+        if (finite) chg[slot] = (int)c;
+    }
+    if (bad) atomicOr(&ctr->err, 1);
+}
+
+// ---------------------------------------------------------------------------
 // compact relative box records
 // ---------------------------------------------------------------------------
 // Byte 2d = lower corner minus the cell's coordinate on dim d (int8; on a

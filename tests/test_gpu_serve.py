@@ -2,9 +2,12 @@
 
 Requests over three systems (2-D, 3-D, 4-D; caller-owned and server-built
 abstractions) are submitted in waves while earlier ones are still on the GPU;
-each result must equal a solo bf_solve of the same inputs, bit for bit.  A
-small memory budget forces the server to build a recompute-mode abstraction,
-and a request that can never fit completes with BF_ERR_OOM.
+each result must equal a solo bf_solve of the same inputs and the CPU oracle's
+solve of the same boxes (exported from the library's builder, or the oracle's
+own boxes imported into the library), bit for bit.  A small memory budget
+forces the server to build a recompute-mode or hybrid abstraction, whose
+results are compared with the oracle too, and a request that can never fit
+completes with BF_ERR_OOM.
 """
 import math
 import time
@@ -12,14 +15,26 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 import paper_2001_06231_gb300 as bf
 from paper_2001_06231_gb300 import workloads as wl
+from parity import import_boxes, oracle_boxes
 
 pytestmark = pytest.mark.gpu
 
 
 def system_of(w):
     return (w.kind, w.params, w.substeps, w.grid, w.inputs, w.tau)
+
+
+def oracle_of(w, boxes, G, tgt):
+    T = np.where(np.asarray(tgt).astype(bool), 0.0, math.inf)
+    return oracle.solve(w.grid.n, w.grid.periodic, boxes, G, T, w.avoid)
+
+
+def same_result(r, ref):
+    return (r["iters"] == ref["iters"] and r["status"] == ref["status"]
+            and np.array_equal(r["V"], ref["V"]) and np.array_equal(r["mu"], ref["mu"]))
 
 
 def test_results_alone_equal_results_in_the_mix():
@@ -37,6 +52,8 @@ def test_results_alone_equal_results_in_the_mix():
             tgt = np.roll(tgt, int(rng.integers(-300, 300)))
             tgt &= 1 - w.avoid
         reqs.append((k, G, tgt))
+    # the oracle's own boxes imported into the library: one request per system in the mix
+    A_orc = [import_boxes(w, oracle_boxes(w)) for w in base]
     srv = bf.Server(hbm_budget=8 << 30, max_active=5, passes_per_step=4)
     ids = []
     for wave in range(3):                                          # later waves join a running engine
@@ -47,16 +64,25 @@ def test_results_alone_equal_results_in_the_mix():
             else:
                 rid = srv.submit(G, target=tgt, avoid=w.avoid, system=system_of(w))
             ids.append(rid)
+        if wave == 1:
+            orc_ids = [srv.submit(w.G, target=w.target, avoid=w.avoid, abstraction=A)
+                       for w, A in zip(base, A_orc)]
         time.sleep(0.01)
     results = [srv.poll(rid, wait=True) for rid in ids]
+    orc_results = [srv.poll(rid, wait=True) for rid in orc_ids]
     srv.close()
     solo_abs = [bf.abs_build_workload(w) for w in base]
+    own_boxes = [A.export_boxes() for A in solo_abs]               # what the server's builder made too
     overlapped = 0
     for (k, G, tgt), r in zip(reqs, results):
         assert r["done"] == 1 and r["error"] == 0
         s = bf.bf_solve(solo_abs[k], G, target=tgt, avoid=base[k].avoid)
-        assert r["iters"] == s["iters"] and r["status"] == s["status"]
-        assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"])
+        assert same_result(r, s)
+        assert same_result(r, oracle_of(base[k], own_boxes[k], G, tgt))
+    for w, r in zip(base, orc_results):
+        assert r["done"] == 1 and r["error"] == 0
+        assert same_result(r, oracle_of(w, oracle_boxes(w), w.G, w.target))
+    results = results + orc_results
     # requests really shared the device: some were admitted before others finished
     for a in results:
         for b in results:
@@ -73,7 +99,10 @@ def test_small_budget_builds_hybrid_or_recompute_mode_and_rejects_oversized():
     refused with BF_ERR_OOM."""
     w = wl.unicycle3d(n=(60, 56, 24), n_obstacles=8)
     C = w.ncells
-    s = bf.bf_solve(bf.abs_build_workload(w), w.G, target=w.target, avoid=w.avoid)
+    S = bf.abs_build_workload(w)
+    s = bf.bf_solve(S, w.G, target=w.target, avoid=w.avoid)
+    ref = oracle_of(w, S.export_boxes(), w.G, w.target)
+    assert same_result(s, ref)
 
     def serve(budget):
         srv = bf.Server(hbm_budget=budget, max_active=2)
@@ -93,7 +122,7 @@ def test_small_budget_builds_hybrid_or_recompute_mode_and_rejects_oversized():
     for budget, mode in ((hi + 1024, bf.MODE_RECOMPUTE), (hi + 1024 + 3 * C * 8, bf.MODE_HYBRID)):
         srv, r = serve(budget)
         assert r["error"] == 0 and r["mode"] == mode, (r["error"], r["mode"], mode)
-        assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"]) and r["iters"] == s["iters"]
+        assert same_result(r, ref)                                  # the oracle on the builder's boxes
         if mode == bf.MODE_RECOMPUTE:
             srv.close()
     big = wl.unicycle3d(n=(200, 200, 64), n_obstacles=0)

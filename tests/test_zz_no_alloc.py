@@ -85,7 +85,7 @@ def test_noalloc_terminal_cost_and_cap():
 def test_noalloc_rejects_oversized_and_host_arrays():
     import torch
     L, f = _entry()
-    n = 2_000_000                                  # ~56 MB of scratch needed > 32 MiB
+    n = 2_000_000                                  # ~96 MB of scratch needed (40 + 8 B per cell) > 32 MiB
     boxes = np.zeros((n, 1, 2, 2), dtype=np.int16)
     A = bf.abs_from_boxes(bf.make_grid([2000, 1000]), boxes)
     G = torch.ones((n, 1), dtype=torch.float64, device="cuda")
