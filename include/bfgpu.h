@@ -181,6 +181,17 @@ BF_API int abs_export_pred(const bf_abstraction *abs, int16_t *out, void *stream
 BF_API int abs_info(const bf_abstraction *abs, int64_t *ncells, int32_t *ninputs,
              int32_t *ndim, int32_t *mode, int64_t *device_bytes, int32_t *box_record_bytes);
 
+/* abs_shape_info -- the plane shape table of an abstraction (stored compact
+ * records on a grid of 2+ dims whose dims 0 and 1 are not periodic).  A plane
+ * is the set of cells with equal coordinates on dims >= 2; for dynamics that
+ * do not depend on the coordinates of dims 0 and 1 (Def. abstraction, built
+ * from one flow for every cell: the unicycle and fire models) all non-blocked
+ * boxes of a plane and input have the same relative record.  *nplanes = the
+ * number of planes (0: no table), *mismatch = the non-blocked boxes whose
+ * record differs from their plane's entry (they are gathered cell by cell).
+ * Either out pointer may be NULL. */
+BF_API int abs_shape_info(const bf_abstraction *abs, int64_t *nplanes, int64_t *mismatch);
+
 /* abs_free -- release an abstraction (NULL is a no-op).  The caller must not
  * free it while a solve on it is running. */
 BF_API void abs_free(bf_abstraction *abs);
@@ -256,15 +267,25 @@ BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *t
              const uint8_t *avoid, const bf_solve_opts *opts, double *V, uint8_t *mu,
              int64_t *iters, int32_t *status, void *stream);
 
-/* bf_tune -- pick the pass schedule of this abstraction's solves by timing:
+/* bf_tune -- pick the pass schedule of this abstraction's solves by timing
+ * (one schedule dimension at a time, keeping the others at the best found so
+ * far, over two rounds):
  * the slice target (inputs of a small frontier's chunks split over warps when
  * the frontier has fewer chunks than slice_target x warps; 0 = never),
  * whether relax marks the next frontier itself or a propagate launch does,
  * the relax grid (one or half a wave) and, on grids of 2 or more dims,
  * whether boxes at least 3 cells wide on dims 0 and 1 read a table of 3 x 3
  * window maxima (fewer gathers, more table upkeep per changed cell; not
- * with a successor class).  Each of the 16 candidates (32 with the window
- * table) is solved three times on the given inputs (G, target, avoid and the
+ * with a successor class) and, where the abstraction has a plane shape table
+ * (stored compact records on 2+ dims, dims 0 and 1 not periodic: the cells
+ * with equal coordinates on dims >= 2 share each input's relative box), whether
+ * a warp whose cells lie on one plane reads that plane's precomputed lookup
+ * offsets instead of decoding each box, and whether the next frontier is
+ * marked from the planes' predecessor templates (the rows of pred(y) of Eq.
+ * (pred) for every cell y of a plane, when every box of a plane and input is
+ * the plane's entry) instead of the per-cell bounding boxes of pred, and
+ * (with the lookup lists) whether relax takes two inputs per iteration.  Each
+ * candidate is solved three times on the given inputs (G, target, avoid and the
  * optional terminal / succ_class / G_class / max_iters of opts; flags, trace
  * and stats are ignored); the fastest stays in force for later bf_solve calls
  * on the handle.  Results never depend on the schedule.  Errors: as bf_solve. */
@@ -276,6 +297,12 @@ typedef struct {
     double best_ms;            /* mean solve time of the chosen schedule          */
     double default_ms;         /* the same for the default schedule               */
     int32_t window33;          /* 1: the 3 x 3 window table is used               */
+    int32_t plane_lists;       /* 1: warps whose cells share a plane read that
+                                  plane's precomputed lookup lists              */
+    int32_t templates;         /* 1: the next frontier is marked from the
+                                  planes' predecessor templates                 */
+    int32_t pair_inputs;       /* 1: with plane lookup lists, relax takes two
+                                  inputs per iteration (both gathers in flight) */
 } bf_tune_result;
 
 BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *target,
@@ -283,9 +310,11 @@ BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *ta
 
 /* bf_set_schedule -- put a pass schedule in force without timing (a schedule
  * bf_tune printed earlier, or a fixed one): slice_target 0..4, fuse_mark,
- * relax_blocks (<= 0 or above one wave: one wave) and window33 of *sched are
- * read, the rest ignored; window33 has no effect on 1-D grids or solves with
- * a successor class.  Results never depend on the schedule.  Returns BF_OK,
+ * relax_blocks (<= 0 or above one wave: one wave), window33, plane_lists,
+ * templates and pair_inputs of *sched are read, the rest ignored; window33 has no effect on
+ * 1-D grids or solves with a successor class, plane_lists none on
+ * abstractions without a plane shape table or solves with a successor class,
+ * templates none on abstractions without templates.  Results never depend on the schedule.  Returns BF_OK,
  * BF_ERR_INVALID (NULL argument, slice_target out of range) or BF_ERR_CUDA /
  * BF_ERR_OOM (the handle's solve workspace could not be set up). */
 BF_API int bf_set_schedule(const bf_abstraction *abs, const bf_tune_result *sched, void *stream);

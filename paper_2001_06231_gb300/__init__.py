@@ -32,7 +32,7 @@ SCHED_AUTO = SCHED_JACOBI
 FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 
 EXPORTED = ["abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes", "abs_export_boxes",
-            "abs_export_pred", "abs_info",
+            "abs_export_pred", "abs_info", "abs_shape_info",
             "abs_free", "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
             "bf_serve_close", "bf_solve_noalloc", "bf_tune", "bf_set_schedule", "bf_last_error"]
 
@@ -75,7 +75,8 @@ class SolveOpts(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("slice_target", ctypes.c_int32), ("fuse_mark", ctypes.c_int32), ("relax_blocks", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
-                ("window33", ctypes.c_int32)]
+                ("window33", ctypes.c_int32), ("plane_lists", ctypes.c_int32), ("templates", ctypes.c_int32),
+                ("pair_inputs", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -117,6 +118,7 @@ def lib():
         L.abs_export_boxes.argtypes = [P, P, P]
         L.abs_export_pred.argtypes = [P, P, P]
         L.abs_info.argtypes = [P, P, P, P, P, P, P]
+        L.abs_shape_info.argtypes = [P, P, P]
         L.abs_free.argtypes = [P]
         L.abs_free.restype = None
         L.bf_solve.argtypes = [P, P, P, P, P, P, P, P, P, P]
@@ -131,7 +133,7 @@ def lib():
         L.bf_set_schedule.argtypes = [P, P, P]
         L.bf_last_error.restype = ctypes.c_char_p
         for name in ("abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes",
-                     "abs_export_boxes", "abs_export_pred", "abs_info",
+                     "abs_export_boxes", "abs_export_pred", "abs_info", "abs_shape_info",
                      "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
                      "bf_solve_noalloc", "bf_tune", "bf_set_schedule"):
             getattr(L, name).restype = ctypes.c_int
@@ -203,6 +205,9 @@ class Abstraction:
         k = ctypes.c_int32()
         _check(lib().abs_stored_inputs(self.handle, ctypes.byref(k)))
         self.stored_inputs = k.value
+        npl, mis = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().abs_shape_info(self.handle, ctypes.byref(npl), ctypes.byref(mis)))
+        self.shape_planes, self.shape_mismatch = npl.value, mis.value
 
     def export_boxes(self, out=None, stream=None):
         if out is None:
@@ -349,10 +354,12 @@ def bf_tune(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0,
     return {k: getattr(res, k) for k, _ in res._fields_}
 
 
-def bf_set_schedule(abstraction, slice_target=2, fuse_mark=1, relax_blocks=0, window33=0, stream=None):
+def bf_set_schedule(abstraction, slice_target=2, fuse_mark=1, relax_blocks=0, window33=0, plane_lists=1,
+                    templates=1, pair_inputs=0, stream=None):
     """Put a pass schedule in force on this abstraction's solves (no timing)."""
     s = TuneResult()
     s.slice_target, s.fuse_mark, s.relax_blocks, s.window33 = slice_target, fuse_mark, relax_blocks, window33
+    s.plane_lists, s.templates, s.pair_inputs = plane_lists, templates, pair_inputs
     _check(lib().bf_set_schedule(abstraction.handle, ctypes.byref(s), _stream(stream)))
 
 

@@ -18,7 +18,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <vector>
 
 #include "bf_internal.cuh"
 #include "dynamics.cuh"
@@ -256,6 +258,105 @@ __global__ void k_build_compact(DynDesc dd, GridDesc g, const double* __restrict
     }
 }
 
+// Plane shape table.  A plane is the set of cells with equal coordinates on
+// dims >= 2 (the whole grid for D = 2); p = x / stride[2].  For dynamics
+// invariant under translation along dims 0 and 1 (the built-in unicycle and
+// fire models, whose right-hand sides do not depend on x and y) every
+// non-blocked pair (x, u) of a plane has the same relative record.  The entry
+// of (plane, input) is picked in two rounds: any non-blocked record (compare
+// and swap into an empty entry), and, where that one is shared by less than
+// half of the pairs, any record that differs from it; the one more pairs
+// share stays.  Records that differ from the entry are counted.
+__device__ __forceinline__ long long plane_of(const GridDesc& g, long long x) {
+    if (g.D <= 2) return 0;
+    return (long long)grid_div(g, 1, grid_div(g, 0, (unsigned)x));
+}
+
+template <int D>
+__device__ __forceinline__ unsigned long long compact_at(const void* compact, long long p) {
+    return D <= 2 ? (unsigned long long)reinterpret_cast<const unsigned*>(compact)[p]
+                  : reinterpret_cast<const unsigned long long*>(compact)[p];
+}
+
+// skip (or NULL): entries whose first pick is kept; other: records equal to it are not picked
+template <int D>
+__global__ void k_shape_pick(GridDesc g, const void* __restrict__ compact, unsigned long long* shape,
+                             const unsigned long long* __restrict__ other, const unsigned char* __restrict__ skip) {
+    const long long total = g.C * g.U;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long x = p - (long long)u * g.C;
+        const unsigned long long rec = compact_at<D>(compact, p);
+        if (((rec >> 8) & 0x7F) == 0) continue;                // blocked
+        const long long e = plane_of(g, x) * g.U + u;
+        if (skip && skip[e]) continue;
+        if (other && rec == other[e]) continue;
+        unsigned long long* q = shape + e;
+        if (*((volatile unsigned long long*)q) == 0ull) atomicCAS(q, 0ull, rec);
+    }
+}
+
+// Per entry the non-blocked pairs (nb, unless NULL) and those whose record is
+// the entry's (hit); one atomic per group of lanes with the same entry.
+template <int D>
+__global__ void k_shape_count(GridDesc g, const void* __restrict__ compact, const unsigned long long* __restrict__ shape,
+                              unsigned* hit, unsigned* nb) {
+    const long long total = g.C * g.U;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long rounds = (total + stride - 1) / stride;
+    const int lane = threadIdx.x & 31;
+    for (long long it = 0; it < rounds; ++it) {
+        const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x + it * stride;
+        long long e = -1;
+        bool h = false;
+        if (p < total) {
+            const int u = (int)(p / g.C);
+            const long long x = p - (long long)u * g.C;
+            const unsigned long long rec = compact_at<D>(compact, p);
+            if (((rec >> 8) & 0x7F) != 0) {
+                e = plane_of(g, x) * g.U + u;
+                h = rec == shape[e];
+            }
+        }
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, e);
+        const unsigned hm = __ballot_sync(0xFFFFFFFFu, h) & grp;
+        if (e >= 0 && lane == __ffs(grp) - 1) {
+            if (nb) atomicAdd(nb + e, (unsigned)__popc(grp));
+            if (hm) atomicAdd(hit + e, (unsigned)__popc(hm));
+        }
+    }
+}
+
+// Keep the second pick where more pairs share it; flag the entries to retry.
+__global__ void k_shape_choose(long long n, unsigned long long* shape, const unsigned long long* __restrict__ second,
+                               const unsigned* __restrict__ hit1, const unsigned* __restrict__ hit2) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        if (second[e] != 0ull && hit2[e] > hit1[e]) shape[e] = second[e];
+}
+
+__global__ void k_shape_retry(long long n, const unsigned* __restrict__ hit, const unsigned* __restrict__ nb,
+                              unsigned char* skip) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        skip[e] = (2ull * hit[e] >= nb[e]) ? 1 : 0;
+}
+
+template <int D>
+__global__ void k_shape_check(GridDesc g, const void* __restrict__ compact, const unsigned long long* shape,
+                              unsigned long long* mismatch) {
+    const long long total = g.C * g.U;
+    unsigned long long bad = 0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(p / g.C);
+        const long long x = p - (long long)u * g.C;
+        const unsigned long long rec = compact_at<D>(compact, p);
+        if (((rec >> 8) & 0x7F) == 0) continue;
+        if (rec != shape[plane_of(g, x) * g.U + u]) ++bad;
+    }
+    if (bad) atomicAdd(mismatch, bad);
+}
+
 __global__ void k_fill_i32(int* a, long long n, int v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -478,6 +579,146 @@ static int to_compact(bf_abstraction* a, cudaStream_t st) {
     }
 }
 
+// The plane shape table of a compact-record abstraction (grids of 2+ dims,
+// dims 0 and 1 not periodic); left NULL otherwise.  Best effort: the solver
+// works without it.
+template <int D>
+static int build_shapes_t(bf_abstraction* a, cudaStream_t st) {
+    const GridDesc& g = a->g;
+    const long long P = g.C / g.stride[2];
+    unsigned long long* shape = nullptr;
+    unsigned long long* d_bad = nullptr;
+    unsigned long long h_bad = 0;
+    const long long n = P * g.U;
+    unsigned long long* second = nullptr;
+    unsigned *hit1 = nullptr, *hit2 = nullptr, *nbk = nullptr;
+    unsigned char* skip = nullptr;
+    BF_CUDA(cudaMalloc((void**)&shape, sizeof(unsigned long long) * n));
+    cudaError_t e = cudaMalloc((void**)&d_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&second, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&hit1, sizeof(unsigned) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&skip, n);
+    if (e == cudaSuccess) {
+        hit2 = hit1 + n;
+        nbk = hit1 + 2 * n;
+        e = cudaMemsetAsync(shape, 0, sizeof(unsigned long long) * n, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(second, 0, sizeof(unsigned long long) * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hit1, 0, sizeof(unsigned) * 3 * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        const int nb = grid_blocks(g.C * g.U, 256);
+        const int ne = grid_blocks(n, 256);
+        k_shape_pick<D><<<nb, 256, 0, st>>>(g, a->d_boxes, shape, nullptr, nullptr);
+        k_shape_count<D><<<nb, 256, 0, st>>>(g, a->d_boxes, shape, hit1, nbk);
+        k_shape_retry<<<ne, 256, 0, st>>>(n, hit1, nbk, skip);
+        k_shape_pick<D><<<nb, 256, 0, st>>>(g, a->d_boxes, second, shape, skip);
+        k_shape_count<D><<<nb, 256, 0, st>>>(g, a->d_boxes, second, hit2, nullptr);
+        k_shape_choose<<<ne, 256, 0, st>>>(n, shape, second, hit1, hit2);
+        k_shape_check<D><<<nb, 256, 0, st>>>(g, a->d_boxes, shape, d_bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof h_bad, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_bad);
+    cudaFree(second);
+    cudaFree(hit1);
+    cudaFree(skip);
+    if (e != cudaSuccess) { cudaFree(shape); return bfh::cuda_fail(e, "plane shape table"); }
+    a->d_shape = shape;
+    a->nplanes = P;
+    a->shape_mismatch = (long long)h_bad;
+    a->bytes += sizeof(unsigned long long) * P * g.U;
+    return BF_OK;
+}
+
+// Predecessor templates from the shape table (host; planes x inputs entries).
+// Every non-blocked pair (x, u) of source plane q has the box x + (rel, w) of
+// the entry S[q][u] (no mismatch), so y in box(x, u) means, per dim d, x_d =
+// y_d - rel_d - j_d with 0 <= j_d < w_d (dims >= 2 wrap on periodic dims):
+// target plane p of y gets, for source plane q, the rows d1 = -(rel1 + j1)
+// with dim-0 offsets -(rel0 + w0 - 1) .. -rel0.  Offsets of one (p, q, d1)
+// from different inputs merge into their bounding range (a superset).  The
+// result holds pred(y) of Eq. (pred) for every y of p; with the blocked pairs
+// it may hold a few more cells, which the algorithm tolerates.
+static int build_templates(bf_abstraction* a, cudaStream_t st) {
+    const GridDesc& g = a->g;
+    const long long P = a->nplanes, U = g.U;
+    std::vector<unsigned long long> S((size_t)(P * U));
+    BF_CUDA(cudaMemcpyAsync(S.data(), a->d_shape, sizeof(unsigned long long) * P * U, cudaMemcpyDeviceToHost, st));
+    BF_CUDA(cudaStreamSynchronize(st));
+    const int n2 = g.D >= 3 ? g.n[2] : 1, n3 = g.D >= 4 ? g.n[3] : 1;
+    std::vector<std::map<std::pair<int, int>, std::pair<int, int>>> tm((size_t)P);
+    for (long long q = 0; q < P; ++q) {
+        const int k2 = (int)(q % n2), k3 = (int)(q / n2);
+        for (long long u = 0; u < U; ++u) {
+            const unsigned long long r = S[(size_t)(q * U + u)];
+            int w[4] = {1, 1, 1, 1}, rel[4] = {0, 0, 0, 0};
+            for (int d = 0; d < g.D; ++d) {
+                w[d] = (int)((r >> (16 * d + 8)) & 0x7F);
+                rel[d] = (int)(signed char)((r >> (16 * d)) & 0xFF);
+            }
+            if (w[0] == 0) continue;                           // no pair of the plane
+            for (int j3 = 0; j3 < w[3]; ++j3) {
+                int t3 = k3 + rel[3] + j3;
+                if (g.D >= 4 && g.periodic[3]) t3 = ((t3 % n3) + n3) % n3;
+                if (t3 < 0 || t3 >= n3) continue;
+                for (int j2 = 0; j2 < w[2]; ++j2) {
+                    int t2 = k2 + rel[2] + j2;
+                    if (g.D >= 3 && g.periodic[2]) t2 = ((t2 % n2) + n2) % n2;
+                    if (t2 < 0 || t2 >= n2) continue;
+                    auto& m = tm[(size_t)(t2 + (long long)n2 * t3)];
+                    for (int j1 = 0; j1 < w[1]; ++j1) {
+                        const int d1 = -(rel[1] + j1), lo = -(rel[0] + w[0] - 1), hi = -rel[0];
+                        auto it = m.find({(int)q, d1});
+                        if (it == m.end()) m[{(int)q, d1}] = {lo, hi};
+                        else it->second = {std::min(it->second.first, lo), std::max(it->second.second, hi)};
+                    }
+                }
+            }
+        }
+    }
+    std::vector<int> ptr((size_t)P + 1, 0);
+    std::vector<int4> ent;
+    for (long long p = 0; p < P; ++p) {
+        const auto& m = tm[(size_t)p];
+        for (auto it = m.begin(); it != m.end(); ++it) {
+            const int q = it->first.first, d1 = it->first.second;
+            const int lo = it->second.first, hi = it->second.second;
+            auto nx = m.find({q, d1 + 1});
+            const int cov = (nx != m.end() && nx->second.first <= lo && nx->second.second >= hi) ? 1 : 0;
+            ent.push_back(make_int4(q, d1, (lo & 0xFFFF) | (hi << 16), cov));
+        }
+        ptr[(size_t)p + 1] = (int)ent.size();
+    }
+    int* dptr = nullptr;
+    int4* dent = nullptr;
+    BF_CUDA(cudaMalloc((void**)&dptr, sizeof(int) * ptr.size()));
+    cudaError_t e = cudaMalloc((void**)&dent, sizeof(int4) * std::max<size_t>(1, ent.size()));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !ent.empty())
+        e = cudaMemcpyAsync(dent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaFree(dptr); cudaFree(dent); return bfh::cuda_fail(e, "predecessor templates"); }
+    a->d_tptr = dptr;
+    a->d_tent = dent;
+    a->tmpl_rows = P ? (double)ent.size() / (double)P : 0.0;
+    a->bytes += sizeof(int) * ptr.size() + sizeof(int4) * ent.size();
+    return BF_OK;
+}
+
+static int build_shapes(bf_abstraction* a, cudaStream_t st) {
+    if (a->box_fmt != kBoxCompact || a->g.D < 2 || a->g.periodic[0] || a->g.periodic[1]) return BF_OK;
+    int rc;
+    switch (a->g.D) {
+        case 2: rc = build_shapes_t<2>(a, st); break;
+        case 3: rc = build_shapes_t<3>(a, st); break;
+        default: rc = build_shapes_t<4>(a, st); break;
+    }
+    if (rc == BF_OK && a->d_shape && a->shape_mismatch == 0) rc = build_templates(a, st);
+    return rc;
+}
+
 static bf_abstraction* new_abs() {
     bf_abstraction* a = new bf_abstraction;
     memset(a, 0, sizeof *a);
@@ -492,6 +733,9 @@ extern "C" void abs_free(bf_abstraction* a) {
     cudaFree(a->d_pred);
     cudaFree(a->d_inputs);
     cudaFree(a->d_rk);
+    cudaFree(a->d_shape);
+    cudaFree(a->d_tptr);
+    cudaFree(a->d_tent);
     delete a;
 }
 
@@ -558,6 +802,7 @@ extern "C" int abs_build(const bf_dynamics* dyn, const bf_grid* grid, const bf_i
         if (e != cudaSuccess) rc = bfh::cuda_fail(e, "abs_build kernels");
     }
     if (rc == BF_OK && mode == BF_MODE_STORED) rc = to_compact(a, st);
+    if (rc == BF_OK && mode == BF_MODE_STORED) rc = build_shapes(a, st);
     if (rc == BF_OK && mode == BF_MODE_RECOMPUTE && g.D >= 3 && dyn->rk4_substeps <= kRkMaxSub) {
         // the RK4 work shared by cells with equal coordinates on dims >= 2
         const long long nkeys = g.C / g.stride[2];
@@ -695,6 +940,7 @@ extern "C" int abs_from_boxes(const bf_grid* grid, int32_t ninputs, const int16_
         if (e != cudaSuccess) rc = bfh::cuda_fail(e, "abs_from_boxes pred");
     }
     if (rc == BF_OK) rc = to_compact(a, st);
+    if (rc == BF_OK) rc = build_shapes(a, st);
     if (rc) { abs_free(a); return rc; }
     *out = a;
     return BF_OK;
@@ -729,6 +975,13 @@ extern "C" int abs_export_pred(const bf_abstraction* a, int16_t* out, void* stre
     cudaStream_t st = (cudaStream_t)stream;
     BF_CUDA(cudaMemcpyAsync(out, a->d_pred, sizeof(short) * 2 * a->g.D * a->g.C, cudaMemcpyDefault, st));
     BF_CUDA(cudaStreamSynchronize(st));
+    return BF_OK;
+}
+
+extern "C" int abs_shape_info(const bf_abstraction* a, int64_t* nplanes, int64_t* mismatch) {
+    if (!a) { bfh::set_error("abs_shape_info: NULL abstraction"); return BF_ERR_INVALID; }
+    if (nplanes) *nplanes = a->d_shape ? a->nplanes : 0;
+    if (mismatch) *mismatch = a->d_shape ? a->shape_mismatch : 0;
     return BF_OK;
 }
 

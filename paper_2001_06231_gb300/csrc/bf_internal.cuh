@@ -222,6 +222,21 @@ struct bf_abstraction {
     void* d_boxes;
     int box_fmt;              // bfk::kBoxWide / kBoxCompact / kBoxRecompute / kBoxHybrid
     int nstored;              // inputs with stored records (U, 0, or in between: hybrid)
+    // plane shape table (compact records, grids of 2+ dims with dims 0 and 1
+    // not periodic): per plane p (the cells with equal coordinates on dims
+    // >= 2) and input u, the relative record shared by the plane's
+    // non-blocked pairs (0: the plane has none) [nplanes][U], or NULL
+    unsigned long long* d_shape;
+    long long nplanes;
+    long long shape_mismatch; // non-blocked records that differ from their plane's entry
+    // predecessor templates (shape table with no mismatch): per target plane p
+    // the rows (source plane q, dim-1 offset d1, dim-0 offsets lo..hi) whose
+    // cells x = (y0 + lo .. y0 + hi, y1 + d1, q) hold pred(y) for every cell
+    // y = (y0, y1, p); entries int4 {q, d1, lo & 0xFFFF | hi << 16, flags},
+    // flags bit 0: row (q, d1 + 1) of the template spans lo..hi too
+    int* d_tptr;              // [nplanes + 1]
+    int4* d_tent;             // [d_tptr[nplanes]]
+    double tmpl_rows;         // mean template entries per plane
     // predecessor index [C][2*D] int16 offsets (x = y + off), empty: lo0 > hi0
     short* d_pred;
     double pred_rows;         // mean dim-0 rows of a predecessor box (cells with one)

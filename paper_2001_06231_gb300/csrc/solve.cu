@@ -38,6 +38,10 @@ struct bf_solve_ws {
     long long* M3 = nullptr;
     long long* M33 = nullptr;       // D >= 2: 3 x 3 windows on dims 0-1 (not with a successor class)
     bool use33 = false;             // gathers read M33 (bf_tune may switch it on)
+    int* poffs_rows = nullptr;      // plane lookup lists [P][U][kPlaneEnt] without / with M33
+    int* poffs_33 = nullptr;
+    bool use_plane = true;          // relax reads the plane lookup lists (when the abstraction has them)
+    bool use_tmpl = true;           // marking reads the predecessor templates (when the abstraction has them)
     unsigned char* mu = nullptr;
     unsigned* fbits = nullptr;
     int* cells = nullptr;
@@ -62,6 +66,8 @@ struct bf_solve_ws {
     cudaGraph_t graph = nullptr;
     int relax_blocks = 0, prop_blocks = 0, compact_blocks = 0;
     int relax_blocks_full = 0;      // one full wave of the relax kernel
+    int pl_blocks_full[2] = {0, 0}; // one full wave of the plane relax kernel (one input / two at a time)
+    bool pair = false;              // the plane relax kernel takes two inputs per iteration
     int slice_target = kSliceTarget;
     bool tuned = false;             // bf_tune chose the schedule below
     bool fuse_mark = true;          // relax marks F2 (no propagate launch per pass)
@@ -89,6 +95,7 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->cand_key); cudaFree(w->cand_u); cudaFree(w->slice_cnt);
     cudaFree(w->rmask); cudaFree(w->GRint); cudaFree(w->VN); cudaFree(w->VR); cudaFree(w->M2R);
     cudaFree(w->M3R); cudaFree(w->stage_GR);
+    cudaFree(w->poffs_rows); cudaFree(w->poffs_33);
     delete w;
 }
 
@@ -108,6 +115,15 @@ __global__ void k_init_values(long long C, const double* __restrict__ terminal,
                               long long* Vnew, unsigned char* mu, int* chg, int* stamp,
                               Counters* ctr) {
     init_values_body(C, terminal, target, avoid, Vkey, Vnew, mu, chg, stamp, ctr);
+}
+
+// Lookup lists of every (plane, input) of the shape table (thread per entry).
+template <int D>
+__global__ void k_plane_lists(GridDesc g, const unsigned long long* __restrict__ shape, long long P, int m33,
+                              int* out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < P * g.U;
+         e += (long long)gridDim.x * blockDim.x)
+        plane_offsets<D>(g, shape[e], (int)(e / g.U), m33 != 0, out + e * kPlaneEnt);
 }
 
 __global__ void k_init_tables(InstView v) {
@@ -130,6 +146,10 @@ template <int D, int FMT, bool COUNT, bool MARK>
 __global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybrid) ? 2 : 4) k_relax(InstView v) {
     relax_pass<D, FMT, COUNT, MARK, false>(v);
 }
+
+// Relax on abstractions with plane lookup lists (solve_plane.cu).
+int plane_relax_wave(int D, bool pair);
+void launch_relax_plane(const InstView& v, bool count, bool mark, bool pair, int blocks, cudaStream_t st);
 
 // Propagate (warp per changed cell): set F2's bits from the changed list
 // (set-up: the finite cells; the passes mark F2 inside relax).
@@ -249,6 +269,11 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.M2 = w->M2;
     v.M3 = w->M3;
     v.M33 = (w->cls || !w->use33) ? nullptr : w->M33;   // the class tables have no 3 x 3 windows
+    if (!w->cls && w->use_plane) v.poffs = v.M33 ? w->poffs_33 : w->poffs_rows;
+    if (w->use_tmpl && a->d_tent) {
+        v.tptr = a->d_tptr;
+        v.tent = a->d_tent;
+    }
     v.mu = w->mu;
     v.fbits = w->fbits;
     v.cells = w->cells;
@@ -285,6 +310,16 @@ struct PassTimers {
 
 template <int D, int FMT>
 static void launch_relax(bf_solve_ws* w, const InstView& v, cudaStream_t st, bool count) {
+    if constexpr (FMT == kBoxCompact && D >= 2) {
+        const int full = w->pl_blocks_full[w->pair && !count ? 1 : 0];
+        if (v.poffs && v.g.U <= kPlaneUMax && full > 0) {
+            // the same share of its own wave as the generic kernel's grid
+            int b = (int)(((long long)w->relax_blocks * full + w->relax_blocks_full - 1) / w->relax_blocks_full);
+            if (b < 1) b = 1;
+            launch_relax_plane(v, count, w->fuse_mark, w->pair, b, st);
+            return;
+        }
+    }
     if (w->fuse_mark) {
         if (count) k_relax<D, FMT, true, true><<<w->relax_blocks, 256, 0, st>>>(v);
         else k_relax<D, FMT, false, true><<<w->relax_blocks, 256, 0, st>>>(v);
@@ -338,6 +373,10 @@ static void launch_setup_frontier(const bf_abstraction* a, bf_solve_ws* w, const
 
 template <int D>
 static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
+    if (D >= 2 && a->box_fmt == kBoxCompact && a->d_shape && a->g.U <= kPlaneUMax) {
+        w->pl_blocks_full[0] = plane_relax_wave(D, false);
+        w->pl_blocks_full[1] = plane_relax_wave(D, true);
+    }
     switch (a->box_fmt) {
         case kBoxCompact: w->relax_blocks = full_wave(k_relax<D, kBoxCompact, false, true>, 256); break;
         case kBoxRecompute: w->relax_blocks = full_wave(k_relax<D, kBoxRecompute, false, true>, 256); break;
@@ -347,7 +386,7 @@ static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
     w->prop_blocks = full_wave(k_propagate<D>, 256);
     // marking inside relax pays when predecessor boxes are small: the marks
     // then cost less than a separate launch per pass (bf_tune may override)
-    if (!w->tuned) w->fuse_mark = a->pred_rows <= kFuseMarkRows;
+    if (!w->tuned) w->fuse_mark = (a->d_tent ? a->tmpl_rows : a->pred_rows) <= kFuseMarkRows;
     w->compact_blocks = blocks_for(w->nwords, 256);
 }
 
@@ -363,7 +402,39 @@ static int ws_blocks(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
     // slice buffers: a sliced pass has nchunks < slice_target x warps and
     // fewer than 2 x slice_target x warps (chunk, slice) items
     w->relax_blocks_full = w->relax_blocks;
-    const long long warps = (long long)w->relax_blocks * 8;
+    if (a->d_shape && !w->poffs_rows) {
+        const long long n = a->nplanes * a->g.U;
+        cudaError_t e = cudaMalloc((void**)&w->poffs_rows, sizeof(int) * kPlaneEnt * n);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&w->poffs_33, sizeof(int) * kPlaneEnt * n);
+        if (e == cudaSuccess) {
+            const int nb = blocks_for(n, 128);
+            switch (a->g.D) {
+                case 2:
+                    k_plane_lists<2><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 0, w->poffs_rows);
+                    k_plane_lists<2><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 1, w->poffs_33);
+                    break;
+                case 3:
+                    k_plane_lists<3><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 0, w->poffs_rows);
+                    k_plane_lists<3><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 1, w->poffs_33);
+                    break;
+                default:
+                    k_plane_lists<4><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 0, w->poffs_rows);
+                    k_plane_lists<4><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 1, w->poffs_33);
+                    break;
+            }
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(w->poffs_rows); cudaFree(w->poffs_33);
+            w->poffs_rows = w->poffs_33 = nullptr;
+            w->relax_blocks = 0;
+            return bfh::cuda_fail(e, "plane lookup lists");
+        }
+    }
+    long long warps = w->relax_blocks;
+    for (int i = 0; i < 2; ++i)
+        if (w->pl_blocks_full[i] > warps) warps = w->pl_blocks_full[i];
+    warps *= 8;
     const long long cap = 2LL * kSliceTargetMax * warps * 32;
     cudaError_t e = cudaMalloc((void**)&w->cand_key, sizeof(long long) * cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w->cand_u, sizeof(int) * cap);
@@ -618,12 +689,27 @@ static int tune_time(const bf_abstraction* a, const double* G, const uint8_t* ta
     return rc;
 }
 
-static void set_schedule(bf_solve_ws* w, int slice_target, bool fuse, int blocks, bool use33) {
+struct Sched {
+    int slice = kSliceTarget;
+    bool fuse = true;
+    int blocks = 0;
+    bool use33 = false;
+    bool plane = true;
+    bool tmpl = true;
+    bool pair = false;
+};
+
+static bool base_plane_on(const Sched& s) { return s.plane; }
+
+static void set_schedule(bf_solve_ws* w, const Sched& s) {
     std::lock_guard<std::mutex> lock(w->mtx);
-    w->slice_target = slice_target;
-    w->fuse_mark = fuse;
-    w->relax_blocks = blocks;
-    w->use33 = use33 && w->M33 != nullptr;
+    w->slice_target = s.slice;
+    w->fuse_mark = s.fuse;
+    w->relax_blocks = s.blocks;
+    w->use33 = s.use33 && w->M33 != nullptr;
+    w->use_plane = s.plane;
+    w->use_tmpl = s.tmpl;
+    w->pair = s.pair;
     w->tuned = true;
     if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
     if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
@@ -656,37 +742,63 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     if (rc == BF_OK && !w) rc = BF_ERR_CUDA;
     if (rc) { cudaFree(V); cudaFree(mu); return rc; }
     const int full = w->relax_blocks_full;
-    int b_slice = w->slice_target, b_blocks = w->relax_blocks;
-    bool b_fuse = w->fuse_mark, b_33 = w->use33;
+    Sched b;
+    b.slice = w->slice_target;
+    b.fuse = w->fuse_mark;
+    b.blocks = w->relax_blocks;
+    b.use33 = w->use33;
+    b.plane = w->use_plane;
+    b.tmpl = w->use_tmpl;
+    b.pair = w->pair;
     out->default_ms = best;
     int tried = 1;
-    const int slices[4] = {0, 1, 2, kSliceTargetMax};
-    const int n33 = (w->M33 && !(opts && opts->succ_class)) ? 2 : 1;
-    for (int t33 = 0; t33 < n33 && rc == BF_OK; ++t33)
-        for (int si = 0; si < 4 && rc == BF_OK; ++si)
-            for (int f = 0; f < 2 && rc == BF_OK; ++f)
-                for (int bi = 0; bi < 2 && rc == BF_OK; ++bi) {
-                    const int blocks = bi == 0 ? full : (full + 1) / 2;
-                    set_schedule(w, slices[si], f != 0, blocks, t33 != 0);
-                    double ms = 0.0;
-                    rc = tune_time(a, G, target, avoid, &o, V, mu, st, &ms);
-                    ++tried;
-                    if (rc == BF_OK && ms < best) {
-                        best = ms;
-                        b_slice = slices[si];
-                        b_fuse = f != 0;
-                        b_blocks = blocks;
-                        b_33 = t33 != 0;
-                    }
+    const bool cls = opts && opts->succ_class;
+    const bool has33 = w->M33 && !cls, hasp = w->poffs_rows && !cls, hast = a->d_tent != nullptr;
+    // coordinate descent: each dimension's values with the others at the best
+    // so far, two rounds
+    for (int round = 0; round < 2 && rc == BF_OK; ++round) {
+        for (int dim = 0; dim < 7 && rc == BF_OK; ++dim) {
+            const int nval = dim == 0 ? 4 : 2;
+            if ((dim == 3 && !has33) || (dim == 4 && !hasp) || (dim == 5 && !hast)) continue;
+            if (dim == 6 && !(hasp && base_plane_on(b))) continue;
+            const Sched base = b;                              // timed already
+            for (int k = 0; k < nval && rc == BF_OK; ++k) {
+                Sched c = base;
+                const int slices[4] = {0, 1, 2, kSliceTargetMax};
+                switch (dim) {
+                    case 0: c.slice = slices[k]; break;
+                    case 1: c.fuse = k != 0; break;
+                    case 2: c.blocks = k == 0 ? full : (full + 1) / 2; break;
+                    case 3: c.use33 = k != 0; break;
+                    case 4: c.plane = k != 0; break;
+                    case 5: c.tmpl = k != 0; break;
+                    default: c.pair = k != 0; break;
                 }
-    set_schedule(w, b_slice, b_fuse, b_blocks, b_33);
+                if (c.slice == base.slice && c.fuse == base.fuse && c.blocks == base.blocks &&
+                    c.use33 == base.use33 && c.plane == base.plane && c.tmpl == base.tmpl && c.pair == base.pair)
+                    continue;
+                set_schedule(w, c);
+                double ms = 0.0;
+                rc = tune_time(a, G, target, avoid, &o, V, mu, st, &ms);
+                ++tried;
+                if (rc == BF_OK && ms < best) {
+                    best = ms;
+                    b = c;
+                }
+            }
+        }
+    }
+    set_schedule(w, b);
     cudaFree(V);
     cudaFree(mu);
     if (rc) return rc;
-    out->slice_target = b_slice;
-    out->fuse_mark = b_fuse ? 1 : 0;
-    out->window33 = b_33 ? 1 : 0;
-    out->relax_blocks = b_blocks;
+    out->slice_target = b.slice;
+    out->fuse_mark = b.fuse ? 1 : 0;
+    out->window33 = b.use33 && w->M33 ? 1 : 0;
+    out->relax_blocks = b.blocks;
+    out->plane_lists = (b.plane && hasp) ? 1 : 0;
+    out->templates = (b.tmpl && hast) ? 1 : 0;
+    out->pair_inputs = (b.pair && b.plane && hasp) ? 1 : 0;
     out->candidates = tried;
     out->best_ms = best;
     return BF_OK;
@@ -711,6 +823,14 @@ extern "C" int bf_set_schedule(const bf_abstraction* a, const bf_tune_result* sc
     }
     int blocks = sched->relax_blocks;
     if (blocks <= 0 || blocks > w->relax_blocks_full) blocks = w->relax_blocks_full;
-    set_schedule(w, st_, sched->fuse_mark != 0, blocks, sched->window33 != 0);
+    Sched c;
+    c.slice = st_;
+    c.fuse = sched->fuse_mark != 0;
+    c.blocks = blocks;
+    c.use33 = sched->window33 != 0;
+    c.plane = sched->plane_lists != 0;
+    c.tmpl = sched->templates != 0;
+    c.pair = sched->pair_inputs != 0;
+    set_schedule(w, c);
     return BF_OK;
 }

@@ -75,6 +75,14 @@ struct InstView {
     const double* inputs;       // [U][udim] (recompute mode)
     const double* rk;           // [keys][U][kRkEntry] shared RK4 parts (recompute mode) or NULL
     const short* pred;          // [C][2D] predecessor offsets
+    // plane lookup lists (compact records, grids of 2+ dims): per (plane,
+    // input) the record every non-blocked pair of the plane shares and the
+    // offsets of its box's table lookups (plane_offsets), or NULL
+    const unsigned long long* shape;   // [P][U]
+    const int* poffs;                  // [P][U][kPlaneEnt]
+    // predecessor templates per target plane (marking), or NULL: bounding boxes
+    const int* tptr;                   // [P + 1]
+    const int4* tent;
     const double* Gint;         // [U][C] running cost, +inf on avoid cells
     long long* Vkey;            // [C]
     long long* Vnew;            // [C]
@@ -108,6 +116,12 @@ struct InstView {
     long long* M3R;
 };
 
+// Plane lookup list entry: int 0 = L | table << 8 (L = 0: no list, the
+// lanes take the general gather), ints 4 .. 4 + L4 - 1 the offsets of the L
+// lookups from the cell, L4 = L rounded up to 4 (padded with the first).
+constexpr int kPlaneEnt = 4 + 28;
+constexpr int kPlaneMaxLook = 28;
+
 // Slices: a pass whose frontier has fewer than slice_target x (warps of the
 // relax grid) chunks splits the inputs of each chunk over several warps
 // (slice_target 0: never).  kSliceTarget is the default, kSliceTargetMax the
@@ -133,6 +147,10 @@ inline void view_from_abs(InstView& v, const bf_abstraction* a) {
     v.inputs = a->d_inputs;
     v.rk = a->d_rk;
     v.pred = a->d_pred;
+    v.shape = a->d_shape;
+    v.poffs = nullptr;            // set by the solve that built the lists
+    v.tptr = nullptr;             // set by the solve when it marks with templates
+    v.tent = nullptr;
 }
 
 // ---------------------------------------------------------------------------
@@ -374,6 +392,62 @@ __device__ __forceinline__ long long box_max_rows(const InstView& v, long long c
     return max(m0, m1);
 }
 
+// Plane of cell x: its coordinates on dims >= 2 as one index (0 for D = 2).
+template <int D>
+__device__ __forceinline__ int plane_of_cell(const GridDesc& g, long long x) {
+    if constexpr (D <= 2) return 0;
+    else return (int)grid_div(g, 1, grid_div(g, 0, (unsigned)x));
+}
+
+// Lookup list of record r on plane p (the lookups box_max_rows makes for a
+// lane of that plane, as offsets from the cell); the table is M33 when m33
+// and the box is at least 3 cells wide on dims 0 and 1, else V / M2 / M3 by
+// the width on dim 0.  Dims 0 and 1 are not periodic here; periodic dims >= 2
+// wrap with the plane's coordinates.
+template <int D>
+__device__ __forceinline__ void plane_offsets(const GridDesc& g, unsigned long long r, int p, bool m33, int* out) {
+    out[0] = 0;
+    if ((rec_byte(r, 1) & 0x7F) == 0) return;                 // no pair of the plane
+    int w[4] = {1, 1, 1, 1}, rel[4] = {0, 0, 0, 0}, k[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        w[d] = rec_byte(r, 2 * d + 1) & 0x7F;
+        rel[d] = rec_sbyte(r, 2 * d);
+    }
+    if (D >= 3) { k[2] = p % g.n[2]; k[3] = p / g.n[2]; }
+    const bool use33 = m33 && D >= 2 && w[0] >= 3 && w[1] >= 3;
+    const int tab = use33 ? 3 : (w[0] == 1 ? 0 : (w[0] == 2 ? 1 : 2));
+    const int np = w[0] < 3 ? 1 : (w[0] + 2) / 3;
+    const int n1 = use33 ? (w[1] + 2) / 3 : w[1];
+    const long long L = (long long)np * n1 * w[2] * w[3];
+    if (L > kPlaneMaxLook) return;
+    int lo[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int d = 2; d < D; ++d) {
+        int x = k[d] + rel[d];
+        if (g.periodic[d]) x = ((x % g.n[d]) + g.n[d]) % g.n[d];
+        lo[d] = x;
+    }
+    int i = 0;
+    for (int j3 = 0; j3 < w[3]; ++j3)
+        for (int j2 = 0; j2 < w[2]; ++j2)
+            for (int j1 = 0; j1 < n1; ++j1)
+                for (int q = 0; q < np; ++q) {
+                    int off = rel[0] + (w[0] < 3 ? 0 : min(3 * q, w[0] - 3));
+                    off += (rel[1] + (use33 ? min(3 * j1, w[1] - 3) : j1)) * (int)g.stride[1];
+                    const int j[4] = {0, 0, j2, j3};
+#pragma unroll
+                    for (int d = 2; d < D; ++d) {
+                        int x = lo[d] + j[d];
+                        if (g.periodic[d] && x >= g.n[d]) x -= g.n[d];
+                        off += (x - k[d]) * (int)g.stride[d];
+                    }
+                    out[4 + i++] = off;
+                }
+    for (; i & 3; ++i) out[4 + i] = out[4];
+    out[0] = (int)L | (tab << 8);
+}
+
 // Does the box hold a cell whose stamp equals `want` (counting mode)?
 template <int D>
 __device__ __forceinline__ bool box_has_stamp(const int* __restrict__ stamp, const GridDesc& g,
@@ -457,6 +531,33 @@ __device__ __forceinline__ void mark_box_rows(const InstView& v, const int* lo, 
     }
 }
 
+// Set the bits of pred of the run of changed cells y0 .. y0 + L - 1 on row y1
+// of plane p from p's predecessor template (dims 0 and 1 not periodic): per
+// entry (q, d1, lo, hi) the cells y0 + lo .. y0 + L - 1 + hi of row y1 + d1 of
+// plane q, clipped to the grid.  skip_cov: the warp already marked the run
+// y0 .. y0 + L - 1 on row y1 - 1 of the same plane, which covered every entry
+// whose flag says row d1 + 1 spans its range.  Lanes take entries.
+__device__ __forceinline__ void mark_template(const InstView& v, int p, int y0, int L, int y1, bool skip_cov) {
+    const int lane = threadIdx.x & 31;
+    const int n0 = v.g.n[0], n1 = v.g.n[1];
+    const int b = __ldg(v.tptr + p), e = __ldg(v.tptr + p + 1);
+    for (int i = b + lane; i < e; i += 32) {
+        const int4 t = __ldg(v.tent + i);
+        if (skip_cov && (t.w & 1)) continue;
+        const int r = y1 + t.y;
+        if (r < 0 || r >= n1) continue;
+        const int lo = (int)(short)(t.z & 0xFFFF), hi = t.z >> 16;
+        const int a = max(0, y0 + lo), z = min(n0 - 1, y0 + L - 1 + hi);
+        if (a > z) continue;
+        const int base = (t.x * n1 + r) * n0;
+        const int ca = base + a, cz = base + z;
+        for (int wd = ca >> 5; wd <= (cz >> 5); ++wd) {
+            const int lo_b = max(ca, wd << 5), hi_b = min(cz, (wd << 5) + 31);
+            mark_word(v.fbits, wd, bit_range(lo_b & 31, hi_b & 31));
+        }
+    }
+}
+
 // Changed cells that follow each other along a dim-0 row, in consecutive
 // places of the changed list, form a run.  propagate_entry(i) commits
 // chg[i]; when chg[i] starts a run, it also sets the bits of the bounding box
@@ -477,6 +578,23 @@ __device__ __forceinline__ void propagate_entry(const InstView& v, int i, int nc
     }
     const int k0 = y0 - (int)grid_div(g, 0, (unsigned)y0) * n0;
     if (i > 0 && k0 != 0 && v.chg[i - 1] == y0 - 1) return;     // inside a run
+    if (v.tent) {
+        // the run's length, 32 places at a time
+        int L = 0;
+        for (int off = 0;; off += 32) {
+            const int idx = i + off + lane;
+            const int y = idx < nchg ? v.chg[idx] : -1;
+            const bool in = y >= 0 && y == y0 + off + lane && k0 + off + lane < n0;
+            const unsigned inm = __ballot_sync(0xFFFFFFFFu, in);
+            const unsigned runm = ~inm ? (inm & ((1u << (__ffs(~inm) - 1)) - 1u)) : inm;
+            L += __popc(runm);
+            if (runm != 0xFFFFFFFFu) break;
+        }
+        const unsigned rq = grid_div(g, 0, (unsigned)y0);
+        const int y1 = (int)(rq - grid_div(g, 1, rq) * (unsigned)g.n[1]);
+        mark_template(v, plane_of_cell<D>(g, y0), k0, L, y1, false);
+        return;
+    }
     // gather the run 32 places at a time; per lane min / max of the box ends
     int mn[D], mx[D];
 #pragma unroll
@@ -553,6 +671,28 @@ __device__ __forceinline__ void mark_changed(const InstView& v, int y, bool chan
     const bool cont = has && lane > 0 && hprev && y == yprev + 1 && ky[0] != 0;
     const unsigned contm = __ballot_sync(0xFFFFFFFFu, cont);
     unsigned heads = __ballot_sync(0xFFFFFFFFu, has && !cont);
+    if constexpr (D >= 2) {
+        if (v.tent) {
+            // predecessor templates: per run its plane, row and x range; a run
+            // on the next dim-1 row of the previous run's plane with the same x
+            // range skips the template rows that run already marked
+            const int pl = has ? plane_of_cell<D>(g, y) : 0;
+            int pp = -1, px = -1, pL = -1, py1 = -1;
+            while (heads) {
+                const int h = __ffs(heads) - 1;
+                heads &= heads - 1;
+                const unsigned above = h < 31 ? (contm >> (h + 1)) : 0u;
+                const int L = __ffs(~above);                        // lanes h .. h + L - 1
+                const int x0 = __shfl_sync(0xFFFFFFFFu, ky[0], h);
+                const int y1 = __shfl_sync(0xFFFFFFFFu, ky[1], h);
+                const int p = __shfl_sync(0xFFFFFFFFu, pl, h);
+                const bool cov = p == pp && x0 == px && L == pL && y1 == py1 + 1;
+                mark_template(v, p, x0, L, y1, cov);
+                pp = p; px = x0; pL = L; py1 = y1;
+            }
+            return;
+        }
+    }
     // the previous run's box: when this run's box is the same box moved up by
     // one cell on dim 1 (and no wider on dim 0), the previous box -- marked by
     // this warp -- holds all of it but its top row on dim 1
@@ -786,6 +926,219 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
     }
 }
 
+// Plane kernel (compact records with a plane shape table, at most
+// kPlaneUMax inputs): per warp a shared-memory copy of the lookup lists of the
+// plane its lanes are on, for the inputs the warp relaxes.
+constexpr int kPlaneUMax = 32;
+struct PlaneStage {
+    int ent[kPlaneUMax][kPlaneEnt];
+    unsigned long long rec[kPlaneUMax];
+};
+
+// Copy the lists and records of plane p, inputs u0 .. u1 - 1, into st (whole warp).
+__device__ __forceinline__ void stage_plane(const InstView& v, int p, int u0, int u1, PlaneStage& st) {
+    const int lane = threadIdx.x & 31;
+    const int n = u1 - u0;
+    const int4* src = reinterpret_cast<const int4*>(v.poffs + ((long long)p * v.g.U + u0) * kPlaneEnt);
+    int4* dst = reinterpret_cast<int4*>(&st.ent[0][0]);
+    for (int i = lane; i < n * (kPlaneEnt / 4); i += 32) dst[i] = __ldg(src + i);
+    for (int i = lane; i < n; i += 32) st.rec[i] = __ldg(v.shape + (long long)p * v.g.U + u0 + i);
+    __syncwarp();
+}
+
+// Max over the boxes of the lanes with `mine` set from a staged list.
+__device__ __forceinline__ long long plane_gather_s(const InstView& v, long long c, bool mine, const int* ent,
+                                                    int hdr) {
+    const int L4 = ((hdr & 0xFF) + 3) & ~3;
+    const int tab = hdr >> 8;
+    const long long* t = tab == 3 ? v.M33 : (tab == 2 ? v.M3 : (tab == 1 ? v.M2 : v.Vkey));
+    const long long* base = t + c;
+    const int4* o4 = reinterpret_cast<const int4*>(ent + 4);
+    long long m0 = kKeyMin, m1 = kKeyMin, m2 = kKeyMin, m3 = kKeyMin;
+    for (int i = 0; i < L4; i += 4) {
+        const int4 o = o4[i >> 2];
+        if (mine) {
+            const long long a0 = __ldg(base + o.x), a1 = __ldg(base + o.y);
+            const long long a2 = __ldg(base + o.z), a3 = __ldg(base + o.w);
+            m0 = max(m0, a0);
+            m1 = max(m1, a1);
+            m2 = max(m2, a2);
+            m3 = max(m3, a3);
+        }
+    }
+    return max(max(m0, m1), max(m2, m3));
+}
+
+// Maxima over the boxes of two inputs' lists at once (all loads of a round
+// of four lookups per list are in flight before either max is taken).
+__device__ __forceinline__ void plane_gather2(const InstView& v, long long c, bool ma, const int* ea, int ha, bool mb,
+                                              const int* eb, int hb, long long& ra, long long& rb) {
+    const int La = ((ha & 0xFF) + 3) & ~3, Lb = ((hb & 0xFF) + 3) & ~3;
+    const int ta = ha >> 8, tb = hb >> 8;
+    const long long* pa = (ta == 3 ? v.M33 : (ta == 2 ? v.M3 : (ta == 1 ? v.M2 : v.Vkey))) + c;
+    const long long* pb = (tb == 3 ? v.M33 : (tb == 2 ? v.M3 : (tb == 1 ? v.M2 : v.Vkey))) + c;
+    const int4* oa4 = reinterpret_cast<const int4*>(ea + 4);
+    const int4* ob4 = reinterpret_cast<const int4*>(eb + 4);
+    long long xa = kKeyMin, ya = kKeyMin, xb = kKeyMin, yb = kKeyMin;
+    const int L = La > Lb ? La : Lb;
+    for (int i = 0; i < L; i += 4) {
+        long long a0 = kKeyMin, a1 = kKeyMin, a2 = kKeyMin, a3 = kKeyMin;
+        long long b0 = kKeyMin, b1 = kKeyMin, b2 = kKeyMin, b3 = kKeyMin;
+        if (i < La) {
+            const int4 o = oa4[i >> 2];
+            if (ma) {
+                a0 = __ldg(pa + o.x); a1 = __ldg(pa + o.y);
+                a2 = __ldg(pa + o.z); a3 = __ldg(pa + o.w);
+            }
+        }
+        if (i < Lb) {
+            const int4 o = ob4[i >> 2];
+            if (mb) {
+                b0 = __ldg(pb + o.x); b1 = __ldg(pb + o.y);
+                b2 = __ldg(pb + o.z); b3 = __ldg(pb + o.w);
+            }
+        }
+        xa = max(xa, max(a0, a1));
+        ya = max(ya, max(a2, a3));
+        xb = max(xb, max(b0, b1));
+        yb = max(yb, max(b2, b3));
+    }
+    ra = max(xa, ya);
+    rb = max(xb, yb);
+}
+
+// The box maximum of input u for the lanes of a plane group: the staged list
+// (lanes whose record is the plane's entry), a warp gather of the shared
+// record when its list is too long, or (other records) the box cell by cell.
+template <int D>
+__device__ __forceinline__ long long plane_box_max(const InstView& v, long long c, bool valid, unsigned long long r,
+                                                   const int* ent, int hdr, unsigned long long sr) {
+    const bool match = valid && r == sr;
+    long long m = kKeyMin;
+    if ((hdr & 0xFF) != 0) {
+        if (__any_sync(0xFFFFFFFFu, match)) m = plane_gather_s(v, c, match, ent, hdr);
+    } else {
+        // a list longer than kPlaneMaxLook: one warp gather of the shared record
+        const unsigned mm = __ballot_sync(0xFFFFFFFFu, match);
+        if (mm) {
+            const long long lc = __shfl_sync(0xFFFFFFFFu, (int)c, __ffs(mm) - 1);
+            const long long x = box_max_rows<D>(v, c, match, sr, lc);
+            if (match) m = x;
+        }
+    }
+    if (valid && !match) m = box_max<D>(v.Vkey, v.g, decode_compact<D>(r, v.g, c));
+    return m;
+}
+
+// relax_inputs for a warp whose active lanes' cells lie on planes with
+// lookup lists: lanes are taken plane by plane (a run of 32 frontier cells
+// usually lies on one); a lane whose record is its plane's entry (every
+// non-blocked lane, for dynamics invariant along dims 0 and 1) reads the
+// staged list; any other lane decodes its box and walks it cell by cell.
+// PAIR: inputs go two at a time, the lookups of both in flight together (the
+// comparison still takes them in input order: lowest input among equal
+// minima).
+template <int D, bool COUNT, bool PAIR>
+__device__ __forceinline__ void relax_plane(const InstView& v, long long c, bool act, int u0, int u1,
+                                            long long round, long long& best, int& bu, bool& in_exact,
+                                            PlaneStage& st) {
+    const GridDesc& g = v.g;
+    const int pl = act ? plane_of_cell<D>(g, c) : -1;
+    unsigned pend = __ballot_sync(0xFFFFFFFFu, act);
+    const compact_t<D>* rp = reinterpret_cast<const compact_t<D>*>(v.boxes) + c;
+    const double* gp = v.Gint + c;
+    while (pend) {
+        const int p = __shfl_sync(0xFFFFFFFFu, pl, __ffs(pend) - 1);
+        const bool grp = act && pl == p;
+        pend &= ~__ballot_sync(0xFFFFFFFFu, grp);
+        stage_plane(v, p, u0, u1, st);
+        if constexpr (!PAIR) {
+            // one input at a time; the next input's record and cost are loaded
+            // while this one is gathered
+            unsigned long long nr = grp ? (unsigned long long)__ldcs(rp + (long long)u0 * g.C) : 0ull;
+            double ng = grp ? __ldcs(gp + (long long)u0 * g.C) : 0.0;
+            for (int u = u0; u < u1; ++u) {
+                const unsigned long long r = nr;
+                const double gv = ng;
+                if (u + 1 < u1 && grp) {
+                    nr = (unsigned long long)__ldcs(rp + (long long)(u + 1) * g.C);
+                    ng = __ldcs(gp + (long long)(u + 1) * g.C);
+                }
+                const bool valid = grp && (rec_byte(r, 1) & 0x7F) != 0;
+                if (!__any_sync(0xFFFFFFFFu, valid)) continue;
+                const long long m = plane_box_max<D>(v, c, valid, r, st.ent[u - u0], st.ent[u - u0][0],
+                                                     st.rec[u - u0]);
+                if constexpr (COUNT) {
+                    if (valid && !in_exact)
+                        in_exact = box_has_stamp<D>(v.stamp, g, decode_compact<D>(r, g, c), (int)round - 1);
+                }
+                if (!valid || m == kKeyInf) continue;            // +inf + G = +inf
+                const long long dk = key_of(gv + val_of(m));     // the one FP64 add
+                if (dk < best) { best = dk; bu = u; }
+            }
+            __syncwarp();                                        // before the stage is overwritten
+            continue;
+        }
+        // the next pair's records and costs are loaded while this pair is gathered
+        unsigned long long nr0 = 0ull, nr1 = 0ull;
+        double ng0 = 0.0, ng1 = 0.0;
+        if (grp) {
+            nr0 = (unsigned long long)__ldcs(rp + (long long)u0 * g.C);
+            ng0 = __ldcs(gp + (long long)u0 * g.C);
+            if (u0 + 1 < u1) {
+                nr1 = (unsigned long long)__ldcs(rp + (long long)(u0 + 1) * g.C);
+                ng1 = __ldcs(gp + (long long)(u0 + 1) * g.C);
+            }
+        }
+        for (int u = u0; u < u1; u += 2) {
+            const bool two = u + 1 < u1;
+            const unsigned long long r0 = nr0, r1 = nr1;
+            const double g0 = ng0, g1 = ng1;
+            if (grp) {
+                if (u + 2 < u1) {
+                    nr0 = (unsigned long long)__ldcs(rp + (long long)(u + 2) * g.C);
+                    ng0 = __ldcs(gp + (long long)(u + 2) * g.C);
+                }
+                if (u + 3 < u1) {
+                    nr1 = (unsigned long long)__ldcs(rp + (long long)(u + 3) * g.C);
+                    ng1 = __ldcs(gp + (long long)(u + 3) * g.C);
+                }
+            }
+            const bool v0 = grp && (rec_byte(r0, 1) & 0x7F) != 0;
+            const bool v1 = two && grp && (rec_byte(r1, 1) & 0x7F) != 0;
+            if (!__any_sync(0xFFFFFFFFu, v0 || v1)) continue;
+            const int* e0 = st.ent[u - u0];
+            const int* e1 = st.ent[two ? u + 1 - u0 : u - u0];
+            const int h0 = e0[0], h1 = two ? e1[0] : 0;
+            const unsigned long long s0 = st.rec[u - u0], s1 = two ? st.rec[u + 1 - u0] : 0ull;
+            long long m0 = kKeyMin, m1 = kKeyMin;
+            const bool f0 = v0 && r0 == s0, f1 = v1 && r1 == s1;
+            if ((h0 & 0xFF) != 0 && (h1 & 0xFF) != 0 &&
+                __all_sync(0xFFFFFFFFu, f0 == v0 && f1 == v1)) {
+                plane_gather2(v, c, f0, e0, h0, f1, e1, h1, m0, m1);
+            } else {
+                m0 = plane_box_max<D>(v, c, v0, r0, e0, h0, s0);
+                if (two) m1 = plane_box_max<D>(v, c, v1, r1, e1, h1, s1);
+            }
+            if constexpr (COUNT) {
+                if (v0 && !in_exact)
+                    in_exact = box_has_stamp<D>(v.stamp, g, decode_compact<D>(r0, g, c), (int)round - 1);
+                if (v1 && !in_exact)
+                    in_exact = box_has_stamp<D>(v.stamp, g, decode_compact<D>(r1, g, c), (int)round - 1);
+            }
+            if (v0 && m0 != kKeyInf) {                       // +inf + G = +inf
+                const long long dk = key_of(g0 + val_of(m0));   // the one FP64 add
+                if (dk < best) { best = dk; bu = u; }
+            }
+            if (v1 && m1 != kKeyInf) {
+                const long long dk = key_of(g1 + val_of(m1));
+                if (dk < best) { best = dk; bu = u + 1; }
+            }
+        }
+        __syncwarp();                                        // before the stage is overwritten
+    }
+}
+
 // Write the result of a relaxed cell: Vnew, mu and the changed list; with
 // MARK also the predecessor boxes of the changed cells into the next frontier.
 template <int D, bool COUNT, bool MARK>
@@ -807,15 +1160,17 @@ __device__ __forceinline__ void commit_cell(const InstView& v, long long c, long
 // Returns the number of cells relaxed; in counting mode adds the cells of the
 // exact F1 (some box holds a cell changed in the previous pass) to *exact.
 // MARK: also set the next frontier's bits (no separate propagate launch).
-template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false>
-__device__ __forceinline__ int relax_chunk(const InstView& v, int first, int count, long long round, int* exact) {
+template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false, int PLANE = 0>
+__device__ __forceinline__ int relax_chunk(const InstView& v, int first, int count, long long round, int* exact,
+                                           PlaneStage* st = nullptr) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < count;
     const long long c = act ? v.cells[first + lane] : 0;
     long long best = act ? v.Vkey[c] : 0;
     int bu = -1;
     bool in_exact = false;
-    relax_inputs<D, FMT, COUNT, CLS>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
+    if constexpr (PLANE != 0) relax_plane<D, COUNT, PLANE == 2>(v, c, act, 0, v.g.U, round, best, bu, in_exact, *st);
+    else relax_inputs<D, FMT, COUNT, CLS>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
     commit_cell<D, COUNT, MARK>(v, c, best, bu, in_exact, exact);
     return count < 32 ? count : 32;
 }
@@ -826,9 +1181,9 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
 // smaller candidate -- the same lowest input among the smallest values as one
 // warp going through all inputs -- commits the cells and resets the counter.
 // Returns the cells relaxed (counted by the completing warp).
-template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false>
+template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false, int PLANE = 0>
 __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, int sl, int S, int q, long long round,
-                                           int* exact) {
+                                           int* exact, PlaneStage* st = nullptr) {
     const int lane = threadIdx.x & 31;
     const int first = ch << 5;
     const int count = ncur - first;
@@ -839,7 +1194,8 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
     bool in_exact = false;
     const int u0 = sl * q;
     const int u1 = min(v.g.U, u0 + q);
-    relax_inputs<D, FMT, COUNT, CLS>(v, c, act, u0, u1, round, best, bu, in_exact);
+    if constexpr (PLANE != 0) relax_plane<D, COUNT, PLANE == 2>(v, c, act, u0, u1, round, best, bu, in_exact, *st);
+    else relax_inputs<D, FMT, COUNT, CLS>(v, c, act, u0, u1, round, best, bu, in_exact);
     const long long base = (long long)ch * S * 32 + lane;
     v.cand_key[base + (long long)sl * 32] = best;
     v.cand_u[base + (long long)sl * 32] = (bu < 0 ? 0xFFFF : bu) | (in_exact ? 1 << 16 : 0);
@@ -867,7 +1223,7 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
 
 // One relax launch of the single solve (whole grid): warps take the chunks
 // of 32 frontier cells, or (small frontiers) (chunk, input slice) items.
-template <int D, int FMT, bool COUNT, bool MARK, bool CLS>
+template <int D, int FMT, bool COUNT, bool MARK, bool CLS, int PLANE = 0>
 __device__ __forceinline__ void relax_pass(const InstView& v) {
     Counters* k = v.ctr;
     if (k->done) return;
@@ -888,14 +1244,19 @@ __device__ __forceinline__ void relax_pass(const InstView& v) {
         if ((long long)nchunks * S * 32 > v.slice_cap) { S = 1; q = U; }
     }
     const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    PlaneStage* st = nullptr;
+    if constexpr (PLANE != 0) {
+        extern __shared__ __align__(16) unsigned char plane_smem[];
+        st = reinterpret_cast<PlaneStage*>(plane_smem) + (threadIdx.x >> 5);
+    }
     if (S == 1) {
         for (int ch = gw; ch < nchunks; ch += nwarps)
-            relaxed += relax_chunk<D, FMT, COUNT, MARK, CLS>(v, ch << 5, ncur - (ch << 5), round, &exact);
+            relaxed += relax_chunk<D, FMT, COUNT, MARK, CLS, PLANE>(v, ch << 5, ncur - (ch << 5), round, &exact, st);
     } else {
         const int items = nchunks * S;
         for (int it = gw; it < items; it += nwarps) {
             const int ch = it / S;
-            relaxed += relax_slice<D, FMT, COUNT, MARK, CLS>(v, ncur, ch, it - ch * S, S, q, round, &exact);
+            relaxed += relax_slice<D, FMT, COUNT, MARK, CLS, PLANE>(v, ncur, ch, it - ch * S, S, q, round, &exact, st);
         }
     }
     if ((threadIdx.x & 31) == 0) {
