@@ -24,6 +24,12 @@
 
 using namespace bfk;
 
+// Tile relax for dense passes (solve_tile.cu).
+struct TileState;
+int tile_setup(const bf_abstraction* a, long long* const tables[4], TileState** out);
+void tile_free(TileState* t);
+int launch_relax_tile(const InstView& v, TileState* t, bool mark, cudaStream_t st);
+
 // Mean predecessor-box rows up to which relax marks the next frontier itself.
 constexpr double kFuseMarkRows = 64.0;
 
@@ -68,6 +74,11 @@ struct bf_solve_ws {
     int relax_blocks_full = 0;      // one full wave of the relax kernel
     int pl_blocks_full[2] = {0, 0}; // one full wave of the plane relax kernel (one input / two at a time)
     bool pair = false;              // the plane relax kernel takes two inputs per iteration
+    int dense_pct = 0;              // passes whose F1 holds at least this share (percent) of the
+                                    // cells take the tile relax; 0: never
+    TileState* tile = nullptr;      // tile geometry and tensor maps (set up on first use)
+    bool tile_failed = false;       // the abstraction does not fit the tile form
+    unsigned* f1bits = nullptr;     // [S] F1 as a bitmap (tile relax)
     int slice_target = kSliceTarget;
     bool tuned = false;             // bf_tune chose the schedule below
     bool fuse_mark = true;          // relax marks F2 (no propagate launch per pass)
@@ -96,6 +107,8 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->rmask); cudaFree(w->GRint); cudaFree(w->VN); cudaFree(w->VR); cudaFree(w->M2R);
     cudaFree(w->M3R); cudaFree(w->stage_GR);
     cudaFree(w->poffs_rows); cudaFree(w->poffs_33);
+    cudaFree(w->f1bits);
+    if (w->tile) tile_free(w->tile);
     delete w;
 }
 
@@ -274,6 +287,11 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
         v.tptr = a->d_tptr;
         v.tent = a->d_tent;
     }
+    if (w->dense_pct > 0 && w->tile && !w->cls) {
+        v.f1bits = w->f1bits;
+        v.dense_min = (a->g.C * w->dense_pct + 99) / 100;
+        if (v.dense_min < 1) v.dense_min = 1;
+    }
     v.mu = w->mu;
     v.fbits = w->fbits;
     v.cells = w->cells;
@@ -333,6 +351,8 @@ template <int D>
 static void launch_pass(const bf_abstraction* a, bf_solve_ws* w, const InstView& v, cudaStream_t st,
                         cudaGraphConditionalHandle h, int use_graph, bool count, PassTimers* tm) {
     if (tm) cudaEventRecord(tm->e[0], st);
+    // dense passes: the tile relax (the list relax below then returns at once)
+    if (v.f1bits && !count) launch_relax_tile(v, w->tile, w->fuse_mark, st);
     if (v.rmask) {
         if (count) launch_relax_cls_count(v, w->fuse_mark, w->relax_blocks, st);
         else launch_relax_cls(v, w->fuse_mark, w->relax_blocks, st);
@@ -644,6 +664,10 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
         bfh::set_error("bf_solve: NaN, -inf or |value| > 2^64 in G or the terminal cost");
         return BF_ERR_INVALID;
     }
+    if (hc.fault) {
+        bfh::set_error("bf_solve: the tile relax gave up waiting for its shared-memory copies");
+        return BF_ERR_TIMEOUT;
+    }
     *iters = hc.round;
     *status = hc.status;
     if (opts && opts->stats) {
@@ -651,7 +675,7 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
         // set-up: counters, costs, values, tables, first propagate, first
         // compaction, loop condition (graph); two or three kernels per pass;
         // output
-        o->kernel_launches = (host_loop ? 7 : 8) + (w->fuse_mark ? 2 : 3) * hc.round;
+        o->kernel_launches = (host_loop ? 7 : 8) + ((w->fuse_mark ? 2 : 3) + (v.f1bits && !count ? 1 : 0)) * hc.round;
         o->relaxed_cells = hc.total_relaxed;
         o->executed_pairs = hc.total_relaxed * U;
         o->exact_f1_cells = count ? hc.total_exact : -1;
@@ -689,6 +713,27 @@ static int tune_time(const bf_abstraction* a, const double* G, const uint8_t* ta
     return rc;
 }
 
+// The tile relax's geometry, tensor maps and F1 bitmap (once per workspace);
+// BF_ERR_UNSUPPORTED when the abstraction does not fit the tile form.
+static int ws_tile(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
+    if (w->tile) return BF_OK;
+    if (w->tile_failed) return BF_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(w->mtx);
+    int rc = ws_blocks(a, w, st);
+    if (rc) return rc;
+    long long* tables[4] = {w->Vkey, w->M2, w->M3, w->M33};
+    if (!w->f1bits) {
+        cudaError_t e = cudaMalloc((void**)&w->f1bits, 4 * w->nwords);
+        if (e != cudaSuccess) return bfh::cuda_fail(e, "F1 bitmap");
+    }
+    rc = tile_setup(a, tables, &w->tile);
+    if (rc) {
+        w->tile_failed = true;
+        w->tile = nullptr;
+    }
+    return rc;
+}
+
 struct Sched {
     int slice = kSliceTarget;
     bool fuse = true;
@@ -697,6 +742,7 @@ struct Sched {
     bool plane = true;
     bool tmpl = true;
     bool pair = false;
+    int dense = 0;
 };
 
 static bool base_plane_on(const Sched& s) { return s.plane; }
@@ -710,6 +756,7 @@ static void set_schedule(bf_solve_ws* w, const Sched& s) {
     w->use_plane = s.plane;
     w->use_tmpl = s.tmpl;
     w->pair = s.pair;
+    w->dense_pct = s.dense;
     w->tuned = true;
     if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
     if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
@@ -750,15 +797,18 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     b.plane = w->use_plane;
     b.tmpl = w->use_tmpl;
     b.pair = w->pair;
+    b.dense = w->dense_pct;
     out->default_ms = best;
     int tried = 1;
     const bool cls = opts && opts->succ_class;
     const bool has33 = w->M33 && !cls, hasp = w->poffs_rows && !cls, hast = a->d_tent != nullptr;
+    const bool hasd = !cls && ws_tile(a, w, st) == BF_OK;
     // coordinate descent: each dimension's values with the others at the best
     // so far, two rounds
     for (int round = 0; round < 2 && rc == BF_OK; ++round) {
-        for (int dim = 0; dim < 7 && rc == BF_OK; ++dim) {
-            const int nval = dim == 0 ? 4 : 2;
+        for (int dim = 0; dim < 8 && rc == BF_OK; ++dim) {
+            const int nval = (dim == 0 || dim == 7) ? (dim == 0 ? 4 : 3) : 2;
+            if (dim == 7 && !hasd) continue;
             if ((dim == 3 && !has33) || (dim == 4 && !hasp) || (dim == 5 && !hast)) continue;
             if (dim == 6 && !(hasp && base_plane_on(b))) continue;
             const Sched base = b;                              // timed already
@@ -772,10 +822,12 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
                     case 3: c.use33 = k != 0; break;
                     case 4: c.plane = k != 0; break;
                     case 5: c.tmpl = k != 0; break;
-                    default: c.pair = k != 0; break;
+                    case 6: c.pair = k != 0; break;
+                    default: c.dense = k == 0 ? 0 : (k == 1 ? 15 : 35); break;
                 }
                 if (c.slice == base.slice && c.fuse == base.fuse && c.blocks == base.blocks &&
-                    c.use33 == base.use33 && c.plane == base.plane && c.tmpl == base.tmpl && c.pair == base.pair)
+                    c.use33 == base.use33 && c.plane == base.plane && c.tmpl == base.tmpl && c.pair == base.pair &&
+                    c.dense == base.dense)
                     continue;
                 set_schedule(w, c);
                 double ms = 0.0;
@@ -799,6 +851,7 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     out->plane_lists = (b.plane && hasp) ? 1 : 0;
     out->templates = (b.tmpl && hast) ? 1 : 0;
     out->pair_inputs = (b.pair && b.plane && hasp) ? 1 : 0;
+    out->dense_pct = hasd ? b.dense : 0;
     out->candidates = tried;
     out->best_ms = best;
     return BF_OK;
@@ -831,6 +884,12 @@ extern "C" int bf_set_schedule(const bf_abstraction* a, const bf_tune_result* sc
     c.plane = sched->plane_lists != 0;
     c.tmpl = sched->templates != 0;
     c.pair = sched->pair_inputs != 0;
+    c.dense = sched->dense_pct;
+    if (c.dense < 0 || c.dense > 100) {
+        bfh::set_error("bf_set_schedule: dense_pct %d outside 0..100", c.dense);
+        return BF_ERR_INVALID;
+    }
+    if (c.dense > 0 && ws_tile(a, w, (cudaStream_t)stream) != BF_OK) c.dense = 0;
     set_schedule(w, c);
     return BF_OK;
 }

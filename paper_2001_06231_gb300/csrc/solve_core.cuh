@@ -63,7 +63,7 @@ struct Counters {
     unsigned blocks_done;     // blocks of the running compact launch that finished
     int done;                 // loop condition became false
     int status;               // BF_CONVERGED / BF_NEG_CYCLE / BF_ITER_CAP
-    int pad;
+    int fault;                // nonzero: a kernel gave up waiting for its copies (tile relax)
 };
 
 struct InstView {
@@ -97,6 +97,9 @@ struct InstView {
     long long* trace;           // [trace_cap][4] or NULL
     long long trace_cap;
     int* stamp;                 // [C] pass that last changed the cell (counting mode) or NULL
+    unsigned* f1bits;           // [S] the current frontier F1 as a bitmap (tile relax) or NULL
+    long long dense_min;        // passes with at least this many F1 cells take the tile relax
+                                // (the list relax returns at once), else the list relax
     // input slices (small frontiers): per (chunk, slice) lane candidates and
     // per chunk arrival counters; NULL -> one warp per chunk over all inputs
     long long* cand_key;        // [slice_cap]
@@ -1079,29 +1082,30 @@ __device__ __forceinline__ void relax_plane(const InstView& v, long long c, bool
             __syncwarp();                                        // before the stage is overwritten
             continue;
         }
-        // the next pair's records and costs are loaded while this pair is gathered
-        unsigned long long nr0 = 0ull, nr1 = 0ull;
-        double ng0 = 0.0, ng1 = 0.0;
+        // records and costs are loaded two pairs ahead of the pair being gathered
+        unsigned long long nr0 = 0ull, nr1 = 0ull, mr0 = 0ull, mr1 = 0ull;
+        double ng0 = 0.0, ng1 = 0.0, mg0 = 0.0, mg1 = 0.0;
         if (grp) {
-            nr0 = (unsigned long long)__ldcs(rp + (long long)u0 * g.C);
-            ng0 = __ldcs(gp + (long long)u0 * g.C);
-            if (u0 + 1 < u1) {
-                nr1 = (unsigned long long)__ldcs(rp + (long long)(u0 + 1) * g.C);
-                ng1 = __ldcs(gp + (long long)(u0 + 1) * g.C);
-            }
+            const long long C = g.C;
+            nr0 = (unsigned long long)__ldcs(rp + (long long)u0 * C);
+            ng0 = __ldcs(gp + (long long)u0 * C);
+            if (u0 + 1 < u1) { nr1 = (unsigned long long)__ldcs(rp + (long long)(u0 + 1) * C); ng1 = __ldcs(gp + (long long)(u0 + 1) * C); }
+            if (u0 + 2 < u1) { mr0 = (unsigned long long)__ldcs(rp + (long long)(u0 + 2) * C); mg0 = __ldcs(gp + (long long)(u0 + 2) * C); }
+            if (u0 + 3 < u1) { mr1 = (unsigned long long)__ldcs(rp + (long long)(u0 + 3) * C); mg1 = __ldcs(gp + (long long)(u0 + 3) * C); }
         }
         for (int u = u0; u < u1; u += 2) {
             const bool two = u + 1 < u1;
             const unsigned long long r0 = nr0, r1 = nr1;
             const double g0 = ng0, g1 = ng1;
+            nr0 = mr0; nr1 = mr1; ng0 = mg0; ng1 = mg1;
             if (grp) {
-                if (u + 2 < u1) {
-                    nr0 = (unsigned long long)__ldcs(rp + (long long)(u + 2) * g.C);
-                    ng0 = __ldcs(gp + (long long)(u + 2) * g.C);
+                if (u + 4 < u1) {
+                    mr0 = (unsigned long long)__ldcs(rp + (long long)(u + 4) * g.C);
+                    mg0 = __ldcs(gp + (long long)(u + 4) * g.C);
                 }
-                if (u + 3 < u1) {
-                    nr1 = (unsigned long long)__ldcs(rp + (long long)(u + 3) * g.C);
-                    ng1 = __ldcs(gp + (long long)(u + 3) * g.C);
+                if (u + 5 < u1) {
+                    mr1 = (unsigned long long)__ldcs(rp + (long long)(u + 5) * g.C);
+                    mg1 = __ldcs(gp + (long long)(u + 5) * g.C);
                 }
             }
             const bool v0 = grp && (rec_byte(r0, 1) & 0x7F) != 0;
@@ -1227,6 +1231,7 @@ template <int D, int FMT, bool COUNT, bool MARK, bool CLS, int PLANE = 0>
 __device__ __forceinline__ void relax_pass(const InstView& v) {
     Counters* k = v.ctr;
     if (k->done) return;
+    if (!COUNT && v.f1bits && k->ncur >= v.dense_min) return;   // the tile relax takes this pass
     const long long round = k->round;
     const int ncur = k->ncur;
     const int nchunks = (ncur + 31) >> 5;
@@ -1431,6 +1436,7 @@ __device__ __forceinline__ void compact_words(const InstView& v, int w_begin, in
     if (wd < w_end) {
         bits = v.fbits[wd];
         if (bits) v.fbits[wd] = 0u;
+        if (v.f1bits) v.f1bits[wd] = bits;
     }
     const int cnt = __popc(bits);
     int incl = cnt;
