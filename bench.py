@@ -467,6 +467,14 @@ def batched(args):
         executed += r["stats"]["executed_pairs"]
         passes.append(r["iters"])
 
+    # schedules picked by timing: the batched form's (stored on the abstractions)
+    # and each instance's own single-solve schedule for the sequential arm
+    tb = None
+    if not args.no_tune:
+        tb = bf.bf_tune_batch(As, Gs, targets=tgs, avoids=avs, stream=stream)
+        for A, G, tg, av in zip(As, Gs, tgs, avs):
+            bf.bf_tune(A, G, target=tg, avoid=av, stream=stream)
+
     def batch_step():
         return bf.bf_solve_batch(As, Gs, targets=tgs, avoids=avs, Vs=Vs, mus=mus, stream=stream)
 
@@ -513,6 +521,7 @@ def batched(args):
                        "executed_relaxations_per_step": executed, "abs_build_ms": build_s * 1e3},
             "queries_per_s": n / batch_s, "sequential_queries_per_s": n / seq_s,
             "sequential_ms_per_step": seq_s * 1e3, "batched_over_sequential": seq_s / batch_s,
+            "sequential_relaxations_per_s": canonical / seq_s, "batch_schedule": tb,
             "batched_identical_to_solo": identical, "clocks": clocks}
     print(json.dumps(line), flush=True)
 

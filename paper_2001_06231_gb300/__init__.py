@@ -34,7 +34,8 @@ FLAG_HOST_LOOP, FLAG_COUNT_EXACT, FLAG_TIME_KERNELS = 1, 2, 4
 EXPORTED = ["abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes", "abs_export_boxes",
             "abs_export_pred", "abs_info", "abs_shape_info",
             "abs_free", "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
-            "bf_serve_close", "bf_solve_noalloc", "bf_tune", "bf_set_schedule", "bf_last_error"]
+            "bf_serve_close", "bf_solve_noalloc", "bf_tune", "bf_set_schedule", "bf_tune_batch", "bf_set_batch_schedule",
+            "bf_last_error"]
 
 
 class BfError(RuntimeError):
@@ -131,11 +132,14 @@ def lib():
         L.bf_solve_noalloc.argtypes = [P, P, P, P, P, i64, P, P, P, P, P]
         L.bf_tune.argtypes = [P, P, P, P, P, P, P]
         L.bf_set_schedule.argtypes = [P, P, P]
+        L.bf_tune_batch.argtypes = [i32, P, P, P, P, P, i64, P, P]
+        L.bf_set_batch_schedule.argtypes = [P, P]
         L.bf_last_error.restype = ctypes.c_char_p
         for name in ("abs_build", "abs_build_hybrid", "abs_stored_inputs", "abs_from_boxes",
                      "abs_export_boxes", "abs_export_pred", "abs_info", "abs_shape_info",
                      "bf_solve", "bf_solve_batch", "bf_serve_open", "bf_serve_submit", "bf_serve_poll",
-                     "bf_solve_noalloc", "bf_tune", "bf_set_schedule"):
+                     "bf_solve_noalloc", "bf_tune", "bf_set_schedule", "bf_tune_batch",
+                     "bf_set_batch_schedule"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -383,6 +387,28 @@ def bf_solve_batch(abstractions, Gs, targets=None, avoids=None, terminals=None, 
     _check(lib().bf_solve_batch(n, absa, ga, ta, va, tm if terminals is not None else None, int(max_iters),
                                 Va, ma, it, st, _stream(stream)))
     return [{"V": Vs[i], "mu": mus[i], "iters": it[i], "status": st[i]} for i in range(n)]
+
+
+def bf_tune_batch(abstractions, Gs, targets=None, avoids=None, terminals=None, max_iters=0, stream=None):
+    """Time the batched form's schedules on these instances and keep the fastest on the abstractions."""
+    n = len(abstractions)
+    absa = (ctypes.c_void_p * n)(*[a.handle.value for a in abstractions])
+    ga, k1 = _ptr_array(Gs, lambda a: _host(a, np.float64))
+    ta, k2 = _ptr_array(targets if targets is not None else [None] * n, lambda a: _host(a, np.uint8))
+    va, k3 = _ptr_array(avoids if avoids is not None else [None] * n, lambda a: _host(a, np.uint8))
+    tm, k4 = _ptr_array(terminals if terminals is not None else [None] * n, lambda a: _host(a, np.float64))
+    res = TuneResult()
+    _check(lib().bf_tune_batch(n, absa, ga, ta, va, tm if terminals is not None else None, int(max_iters),
+                               ctypes.byref(res), _stream(stream)))
+    return {k: getattr(res, k) for k, _ in res._fields_}
+
+
+def bf_set_batch_schedule(abstraction, fuse_mark=-1, window33=1, plane_lists=1, templates=1, pair_inputs=1):
+    """Put a batched-form schedule in force on this abstraction (no timing)."""
+    s = TuneResult()
+    s.fuse_mark, s.window33, s.plane_lists, s.templates, s.pair_inputs = (fuse_mark, window33, plane_lists,
+                                                                         templates, pair_inputs)
+    _check(lib().bf_set_batch_schedule(abstraction.handle, ctypes.byref(s)))
 
 
 class Server:

@@ -24,6 +24,7 @@
 
 #include "bf_internal.cuh"
 #include "dynamics.cuh"
+#include "solve_core.cuh"
 
 using namespace bfk;
 
@@ -341,6 +342,15 @@ __global__ void k_shape_retry(long long n, const unsigned* __restrict__ hit, con
         skip[e] = (2ull * hit[e] >= nb[e]) ? 1 : 0;
 }
 
+// Lookup lists of every (plane, input) of the shape table (thread per entry).
+template <int D>
+__global__ void k_plane_lists(GridDesc g, const unsigned long long* __restrict__ shape, long long P, int m33,
+                              int* out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < P * g.U;
+         e += (long long)gridDim.x * blockDim.x)
+        plane_offsets<D>(g, shape[e], (int)(e / g.U), m33 != 0, out + e * kPlaneEnt);
+}
+
 template <int D>
 __global__ void k_shape_check(GridDesc g, const void* __restrict__ compact, const unsigned long long* shape,
                               unsigned long long* mismatch) {
@@ -629,6 +639,13 @@ static int build_shapes_t(bf_abstraction* a, cudaStream_t st) {
     a->nplanes = P;
     a->shape_mismatch = (long long)h_bad;
     a->bytes += sizeof(unsigned long long) * P * g.U;
+    // the lookup lists of every entry, for gathers without and with the 3 x 3 windows
+    for (int m33 = 0; m33 < 2; ++m33) {
+        BF_CUDA(cudaMalloc((void**)&a->d_poffs[m33], sizeof(int) * kPlaneEnt * n));
+        k_plane_lists<D><<<grid_blocks(n, 128), 128, 0, st>>>(g, shape, P, m33, a->d_poffs[m33]);
+        BF_CUDA(cudaGetLastError());
+        a->bytes += sizeof(int) * kPlaneEnt * n;
+    }
     return BF_OK;
 }
 
@@ -722,6 +739,7 @@ static int build_shapes(bf_abstraction* a, cudaStream_t st) {
 static bf_abstraction* new_abs() {
     bf_abstraction* a = new bf_abstraction;
     memset(a, 0, sizeof *a);
+    a->bsched = -1;
     cudaGetDevice(&a->device);
     return a;
 }
@@ -734,6 +752,8 @@ extern "C" void abs_free(bf_abstraction* a) {
     cudaFree(a->d_inputs);
     cudaFree(a->d_rk);
     cudaFree(a->d_shape);
+    cudaFree(a->d_poffs[0]);
+    cudaFree(a->d_poffs[1]);
     cudaFree(a->d_tptr);
     cudaFree(a->d_tent);
     delete a;

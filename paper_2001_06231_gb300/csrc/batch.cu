@@ -84,8 +84,10 @@ __global__ void k_b_values(long long C, const double* __restrict__ terminal,
 
 __global__ void k_b_tables(InstView v) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < v.g.C;
-         c += (long long)gridDim.x * blockDim.x)
+         c += (long long)gridDim.x * blockDim.x) {
         table_entry(v, c);
+        if (v.M33) table33_entry(v, c);
+    }
 }
 
 // Set-up tail of one instance: pred of the finite cells -> F2 bits.
@@ -236,6 +238,30 @@ __global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybri
     }
 }
 
+// The group's relax on plane lookup lists (every instance of the group has
+// them): per-warp staging of the lists in dynamic shared memory.
+template <int D, bool MARK, bool PAIR>
+__global__ void __launch_bounds__(256, PAIR ? 3 : 4) k_b_relax_pl(BatchDev b, int g) {
+    const int beg = b.gbeg[g], end = b.gbeg[g + 1];
+    if (beg >= end) return;
+    extern __shared__ __align__(16) unsigned char b_plane_smem[];
+    PlaneStage* st = reinterpret_cast<PlaneStage*>(b_plane_smem) + (threadIdx.x >> 5);
+    const int base = b.scan[beg], total = b.scan[end] - base;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < total; item += nwarps) {
+        const int pos = base + item;
+        const int i = find_instance(b.scan, beg, end, pos);
+        const InstView& v = b.views[i];
+        const int ch = pos - b.scan[i];
+        int exact = 0;
+        const int r = relax_chunk<D, kBoxCompact, false, MARK, false, PAIR ? 2 : 1>(
+            v, ch << 5, v.ctr->ncur - (ch << 5), v.ctr->round, &exact, st);
+        if ((threadIdx.x & 31) == 0 && r)
+            atomicAdd((unsigned long long*)&v.ctr->relaxed, (unsigned long long)r);
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_b_propagate(BatchDev b, int g) {
     const int beg = b.gbeg[g], end = b.gbeg[g + 1];
@@ -331,7 +357,7 @@ size_t Engine::state_bytes(const bf_abstraction* a, bool stage_G, bool stage_T, 
 
 size_t Engine::state_bytes_for(long long Cc, int Uc, bool stage_G, bool stage_T, bool stage_V) {
     const size_t C = (size_t)Cc, U = (size_t)Uc, S = (C + 31) / 32;
-    size_t o = r256(sizeof(Counters)) + 4 * r256(8 * C) + r256(C) + r256(4 * S) + 2 * r256(4 * C) +
+    size_t o = r256(sizeof(Counters)) + 5 * r256(8 * C) + r256(C) + r256(4 * S) + 2 * r256(4 * C) +
                r256(8 * C * U);
     if (stage_G) o += r256(8 * C * U);
     if (stage_T) o += r256(8 * C) + r256(C) + r256(C);   // terminal or target, plus avoid
@@ -365,6 +391,7 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
     const size_t o_vn = o;   o += r256(8 * (size_t)C);
     const size_t o_m2 = o;   o += r256(8 * (size_t)C);
     const size_t o_m3 = o;   o += r256(8 * (size_t)C);
+    const size_t o_m33 = o;  o += r256(8 * (size_t)C);
     const size_t o_mu = o;   o += r256((size_t)C);
     const size_t o_fb = o;   o += r256(4 * (size_t)S);
     const size_t o_cl = o;   o += r256(4 * (size_t)C);
@@ -391,6 +418,14 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
     v.Vnew = reinterpret_cast<long long*>(m + o_vn);
     v.M2 = reinterpret_cast<long long*>(m + o_m2);
     v.M3 = reinterpret_cast<long long*>(m + o_m3);
+    // the batched schedule of the abstraction (bf_tune_batch) or the default
+    const int bs = a->bsched >= 0 ? a->bsched : kBsDefault;
+    if ((bs & kBsWindow33) && a->g.D >= 2) v.M33 = reinterpret_cast<long long*>(m + o_m33);
+    if ((bs & kBsPlane) && a->d_poffs[0]) v.poffs = a->d_poffs[v.M33 ? 1 : 0];
+    if ((bs & kBsTemplates) && a->d_tent) {
+        v.tptr = a->d_tptr;
+        v.tent = a->d_tent;
+    }
     v.mu = m + o_mu;
     v.fbits = reinterpret_cast<unsigned*>(m + o_fb);
     v.cells = reinterpret_cast<int*>(m + o_cl);
@@ -459,16 +494,25 @@ int Engine::rebuild() {
     int ng = 0;
     for (int i = 0; i < n; ++i) {
         const int g = insts_[i]->group;
+        const bf_abstraction* a = insts_[i]->a;
+        const int bs = a->bsched >= 0 ? a->bsched : kBsDefault;
         if (ng == 0 || (group_D_[ng - 1] - 1) * 4 + group_fmt_[ng - 1] != g) {
             group_D_[ng] = g / 4 + 1;
             group_fmt_[ng] = g % 4;
             group_mark_[ng] = true;
+            // the first instance's schedule decides the group's kernels
+            group_fixed_mark_[ng] = !(bs & kBsMarkAuto);
+            if (group_fixed_mark_[ng]) group_mark_[ng] = (bs & kBsMark) != 0;
+            group_plane_[ng] = (bs & kBsPlane) != 0 && group_fmt_[ng] == kBoxCompact && group_D_[ng] >= 2;
+            group_pair_[ng] = (bs & kBsPair) != 0;
             dev_.gbeg[ng] = i;
             ++ng;
         }
-        // relax marks the next frontier itself when every predecessor box of
-        // the group is small (as in the single solve)
-        if (insts_[i]->a->pred_rows > kFuseMarkRowsBatch) group_mark_[ng - 1] = false;
+        // relax marks the next frontier itself when every predecessor box (or
+        // template) of the group is small (as in the single solve)
+        const double rows = insts_[i]->view.tent ? a->tmpl_rows : a->pred_rows;
+        if (!group_fixed_mark_[ng - 1] && rows > kFuseMarkRowsBatch) group_mark_[ng - 1] = false;
+        if (!a->d_poffs[0] || a->g.U > kPlaneUMax) group_plane_[ng - 1] = false;
     }
     dev_.ngroups = ng;
     dev_.gbeg[ng] = n;
@@ -493,7 +537,13 @@ int Engine::rebuild() {
     m += r256(4);
     dev_.step_left = reinterpret_cast<int*>(m);
     host_views_.resize(n);
-    for (int i = 0; i < n; ++i) host_views_[i] = insts_[i]->view;
+    for (int g = 0; g < ng; ++g)
+        for (int i = dev_.gbeg[g]; i < dev_.gbeg[g + 1]; ++i) {
+            host_views_[i] = insts_[i]->view;
+            // the plane kernel reads every instance's lists; the other kernels none
+            InstView& hv = host_views_[i];
+            hv.poffs = group_plane_[g] ? insts_[i]->a->d_poffs[hv.M33 ? 1 : 0] : nullptr;
+        }
     if (n)
         BF_CUDA(cudaMemcpyAsync(dev_.views, host_views_.data(), sizeof(InstView) * n, cudaMemcpyHostToDevice,
                                 st_));
@@ -509,6 +559,14 @@ int Engine::rebuild() {
 }
 
 template <int D, bool MARK>
+static void launch_relax_pl(const BatchDev& b, int g, bool pair, cudaStream_t st) {
+    const size_t sm = 8 * sizeof(PlaneStage);
+    const int blocks = n_sms() * (pair ? 3 : 4);
+    if (pair) k_b_relax_pl<D, MARK, true><<<blocks, 256, sm, st>>>(b, g);
+    else k_b_relax_pl<D, MARK, false><<<blocks, 256, sm, st>>>(b, g);
+}
+
+template <int D, bool MARK>
 static void launch_relax_m(const BatchDev& b, int g, int fmt, int blocks, cudaStream_t st) {
     switch (fmt) {
         case kBoxCompact: k_b_relax<D, kBoxCompact, MARK><<<blocks, 256, 0, st>>>(b, g); break;
@@ -519,7 +577,15 @@ static void launch_relax_m(const BatchDev& b, int g, int fmt, int blocks, cudaSt
 }
 
 template <int D>
-static void launch_relax(const BatchDev& b, int g, int fmt, bool mark, int blocks, cudaStream_t st) {
+static void launch_relax(const BatchDev& b, int g, int fmt, bool mark, bool plane, bool pair, int blocks,
+                         cudaStream_t st) {
+    if constexpr (D >= 2) {
+        if (plane) {
+            if (mark) launch_relax_pl<D, true>(b, g, pair, st);
+            else launch_relax_pl<D, false>(b, g, pair, st);
+            return;
+        }
+    }
     if (mark) launch_relax_m<D, true>(b, g, fmt, blocks, st);
     else launch_relax_m<D, false>(b, g, fmt, blocks, st);
 }
@@ -531,12 +597,12 @@ static void launch_prop(const BatchDev& b, int g, int blocks, cudaStream_t st) {
 
 void Engine::launch_pass(cudaGraphConditionalHandle h, int use_graph) {
     for (int g = 0; g < dev_.ngroups; ++g) {
-        const bool mark = group_mark_[g];
+        const bool mark = group_mark_[g], pl = group_plane_[g], pr = group_pair_[g];
         switch (group_D_[g]) {
-            case 1: launch_relax<1>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
-            case 2: launch_relax<2>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
-            case 3: launch_relax<3>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
-            default: launch_relax<4>(dev_, g, group_fmt_[g], mark, relax_blocks_, st_); break;
+            case 1: launch_relax<1>(dev_, g, group_fmt_[g], mark, false, false, relax_blocks_, st_); break;
+            case 2: launch_relax<2>(dev_, g, group_fmt_[g], mark, pl, pr, relax_blocks_, st_); break;
+            case 3: launch_relax<3>(dev_, g, group_fmt_[g], mark, pl, pr, relax_blocks_, st_); break;
+            default: launch_relax<4>(dev_, g, group_fmt_[g], mark, pl, pr, relax_blocks_, st_); break;
         }
     }
     k_b_plan<<<1, 1024, 0, st_>>>(dev_, 1, h, use_graph);
@@ -740,5 +806,129 @@ extern "C" int bf_solve_batch(int32_t n, const bf_abstraction* const* abs, const
                        first_err);
         return BF_ERR_INVALID;
     }
+    return BF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// schedule tuning of the batched form
+// ---------------------------------------------------------------------------
+static int batch_time(int32_t n, const bf_abstraction* const* abs, const double* const* G,
+                      const uint8_t* const* target, const uint8_t* const* avoid, const double* const* terminal,
+                      int64_t max_iters, double* const* V, uint8_t* const* mu, int64_t* it, int32_t* stv,
+                      cudaStream_t st, double* ms) {
+    int rc = bf_solve_batch(n, abs, G, target, avoid, terminal, max_iters, V, mu, it, stv, st);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    BF_CUDA(cudaEventCreate(&e0));
+    BF_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && rc == BF_OK; ++r) rc = bf_solve_batch(n, abs, G, target, avoid, terminal, max_iters, V, mu, it, stv, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / 2.0;
+    return rc;
+}
+
+extern "C" int bf_tune_batch(int32_t n, const bf_abstraction* const* abs, const double* const* G,
+                             const uint8_t* const* target, const uint8_t* const* avoid,
+                             const double* const* terminal, int64_t max_iters, bf_tune_result* out, void* stream) {
+    if (n <= 0 || !abs || !G || !out) {
+        bfh::set_error("bf_tune_batch: NULL argument or no instance");
+        return BF_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double*> V(n, nullptr);
+    std::vector<uint8_t*> mu(n, nullptr);
+    std::vector<int64_t> it(n);
+    std::vector<int32_t> stv(n);
+    int rc = BF_OK;
+    for (int i = 0; i < n && rc == BF_OK; ++i) {
+        cudaError_t e = cudaMalloc((void**)&V[i], 8 * (size_t)abs[i]->g.C);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&mu[i], (size_t)abs[i]->g.C);
+        if (e != cudaSuccess) rc = bfh::cuda_fail(e, "bf_tune_batch buffers");
+    }
+    std::vector<int> keep(n);
+    for (int i = 0; i < n; ++i) keep[i] = abs[i]->bsched;
+    auto set_all = [&](int bs) {
+        for (int i = 0; i < n; ++i) const_cast<bf_abstraction*>(abs[i])->bsched = bs;
+    };
+    double best = 0.0;
+    int tried = 0;
+    int b = kBsDefault;
+    if (rc == BF_OK) {
+        set_all(-1);
+        rc = batch_time(n, abs, G, target, avoid, terminal, max_iters, V.data(), mu.data(), it.data(), stv.data(),
+                        st, &best);
+        ++tried;
+    }
+    const double default_ms = best;
+    // coordinate descent over the schedule bits, two rounds; the marking
+    // dimension times both fixed choices against marking by box size
+    const int bits[5] = {kBsMark, kBsWindow33, kBsPlane, kBsTemplates, kBsPair};
+    for (int round = 0; round < 2 && rc == BF_OK; ++round)
+        for (int k = 0; k < 5 && rc == BF_OK; ++k) {
+            const int base = b;
+            int cands[2];
+            if (k == 0) {
+                cands[0] = base & ~(kBsMark | kBsMarkAuto);
+                cands[1] = (base & ~kBsMarkAuto) | kBsMark;
+            } else {
+                cands[0] = base & ~bits[k];
+                cands[1] = base | bits[k];
+            }
+            for (int j = 0; j < 2 && rc == BF_OK; ++j) {
+                const int c = cands[j];
+                if (c == base) continue;
+                set_all(c);
+                double ms = 0.0;
+                rc = batch_time(n, abs, G, target, avoid, terminal, max_iters, V.data(), mu.data(), it.data(),
+                                stv.data(), st, &ms);
+                ++tried;
+                if (rc == BF_OK && ms < best) {
+                    best = ms;
+                    b = c;
+                }
+            }
+        }
+    for (int i = 0; i < n; ++i) {
+        cudaFree(V[i]);
+        cudaFree(mu[i]);
+    }
+    if (rc) {
+        for (int i = 0; i < n; ++i) const_cast<bf_abstraction*>(abs[i])->bsched = keep[i];
+        return rc;
+    }
+    set_all(b);
+    const int bs = b;
+    memset(out, 0, sizeof *out);
+    out->fuse_mark = (bs & kBsMarkAuto) ? -1 : ((bs & kBsMark) ? 1 : 0);
+    out->window33 = (bs & kBsWindow33) ? 1 : 0;
+    out->plane_lists = (bs & kBsPlane) ? 1 : 0;
+    out->templates = (bs & kBsTemplates) ? 1 : 0;
+    out->pair_inputs = (bs & kBsPair) ? 1 : 0;
+    out->candidates = tried;
+    out->best_ms = best;
+    out->default_ms = default_ms;
+    return BF_OK;
+}
+
+extern "C" int bf_set_batch_schedule(bf_abstraction* a, const bf_tune_result* sched) {
+    if (!a || !sched) {
+        bfh::set_error("bf_set_batch_schedule: NULL argument");
+        return BF_ERR_INVALID;
+    }
+    if (sched->fuse_mark < -1 || sched->fuse_mark > 1) {
+        bfh::set_error("bf_set_batch_schedule: fuse_mark must be -1, 0 or 1");
+        return BF_ERR_INVALID;
+    }
+    int bs = (sched->window33 ? kBsWindow33 : 0) | (sched->plane_lists ? kBsPlane : 0) |
+             (sched->templates ? kBsTemplates : 0) | (sched->pair_inputs ? kBsPair : 0);
+    if (sched->fuse_mark == 1) bs |= kBsMark;
+    if (sched->fuse_mark == -1) bs |= kBsMarkAuto;
+    a->bsched = bs;
     return BF_OK;
 }

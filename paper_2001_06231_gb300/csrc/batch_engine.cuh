@@ -106,6 +106,9 @@ private:
     int relax_blocks_ = 0, prop_blocks_ = 0, compact_blocks_ = 0;
     int group_D_[kMaxGroups] = {}, group_fmt_[kMaxGroups] = {};
     bool group_mark_[kMaxGroups] = {};   // relax marks the next frontier (no propagate launch)
+    bool group_fixed_mark_[kMaxGroups] = {};   // ... as the first instance's batched schedule says
+    bool group_plane_[kMaxGroups] = {};  // relax reads the plane lookup lists (plane kernel)
+    bool group_pair_[kMaxGroups] = {};   // ... two inputs per iteration
     // bounded-step graphs of the current instance set, by pass count
     cudaGraphExec_t step_exec_[2] = {nullptr, nullptr};
     int step_passes_[2] = {0, 0};

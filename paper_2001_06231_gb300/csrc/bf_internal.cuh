@@ -229,6 +229,8 @@ struct bf_abstraction {
     unsigned long long* d_shape;
     long long nplanes;
     long long shape_mismatch; // non-blocked records that differ from their plane's entry
+    int* d_poffs[2];          // lookup lists of every (plane, input) without / with the 3 x 3
+                              // window table [nplanes][U][kPlaneEnt] (solve_core.cuh), or NULL
     // predecessor templates (shape table with no mismatch): per target plane p
     // the rows (source plane q, dim-1 offset d1, dim-0 offsets lo..hi) whose
     // cells x = (y0 + lo .. y0 + hi, y1 + d1, q) hold pred(y) for every cell
@@ -242,7 +244,17 @@ struct bf_abstraction {
     double pred_rows;         // mean dim-0 rows of a predecessor box (cells with one)
     size_t bytes;
     bf_solve_ws* ws;          // cached workspace of bf_solve
+    int bsched;               // batched-engine schedule (kBs* bits; bf_tune_batch), -1: default
 };
+
+// batched-engine schedule bits (bf_abstraction::bsched)
+constexpr int kBsWindow33 = 1;    // gathers read the 3 x 3 window table
+constexpr int kBsPlane = 2;       // relax reads the plane lookup lists
+constexpr int kBsTemplates = 4;   // marking reads the predecessor templates
+constexpr int kBsPair = 8;        // plane relax takes two inputs per iteration
+constexpr int kBsMark = 16;       // relax marks the next frontier (else a propagate launch)
+constexpr int kBsMarkAuto = 32;   // ... when the group's predecessor boxes are small (kBsMark ignored)
+constexpr int kBsDefault = kBsWindow33 | kBsPlane | kBsTemplates | kBsPair | kBsMarkAuto;
 
 namespace bfh {
 // thread-local error message (bf_last_error)

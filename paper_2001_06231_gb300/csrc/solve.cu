@@ -44,8 +44,6 @@ struct bf_solve_ws {
     long long* M3 = nullptr;
     long long* M33 = nullptr;       // D >= 2: 3 x 3 windows on dims 0-1 (not with a successor class)
     bool use33 = false;             // gathers read M33 (bf_tune may switch it on)
-    int* poffs_rows = nullptr;      // plane lookup lists [P][U][kPlaneEnt] without / with M33
-    int* poffs_33 = nullptr;
     bool use_plane = true;          // relax reads the plane lookup lists (when the abstraction has them)
     bool use_tmpl = true;           // marking reads the predecessor templates (when the abstraction has them)
     unsigned char* mu = nullptr;
@@ -106,7 +104,6 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->cand_key); cudaFree(w->cand_u); cudaFree(w->slice_cnt);
     cudaFree(w->rmask); cudaFree(w->GRint); cudaFree(w->VN); cudaFree(w->VR); cudaFree(w->M2R);
     cudaFree(w->M3R); cudaFree(w->stage_GR);
-    cudaFree(w->poffs_rows); cudaFree(w->poffs_33);
     cudaFree(w->f1bits);
     if (w->tile) tile_free(w->tile);
     delete w;
@@ -128,15 +125,6 @@ __global__ void k_init_values(long long C, const double* __restrict__ terminal,
                               long long* Vnew, unsigned char* mu, int* chg, int* stamp,
                               Counters* ctr) {
     init_values_body(C, terminal, target, avoid, Vkey, Vnew, mu, chg, stamp, ctr);
-}
-
-// Lookup lists of every (plane, input) of the shape table (thread per entry).
-template <int D>
-__global__ void k_plane_lists(GridDesc g, const unsigned long long* __restrict__ shape, long long P, int m33,
-                              int* out) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < P * g.U;
-         e += (long long)gridDim.x * blockDim.x)
-        plane_offsets<D>(g, shape[e], (int)(e / g.U), m33 != 0, out + e * kPlaneEnt);
 }
 
 __global__ void k_init_tables(InstView v) {
@@ -282,7 +270,7 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.M2 = w->M2;
     v.M3 = w->M3;
     v.M33 = (w->cls || !w->use33) ? nullptr : w->M33;   // the class tables have no 3 x 3 windows
-    if (!w->cls && w->use_plane) v.poffs = v.M33 ? w->poffs_33 : w->poffs_rows;
+    if (!w->cls && w->use_plane) v.poffs = a->d_poffs[v.M33 ? 1 : 0];
     if (w->use_tmpl && a->d_tent) {
         v.tptr = a->d_tptr;
         v.tent = a->d_tent;
@@ -422,35 +410,6 @@ static int ws_blocks(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
     // slice buffers: a sliced pass has nchunks < slice_target x warps and
     // fewer than 2 x slice_target x warps (chunk, slice) items
     w->relax_blocks_full = w->relax_blocks;
-    if (a->d_shape && !w->poffs_rows) {
-        const long long n = a->nplanes * a->g.U;
-        cudaError_t e = cudaMalloc((void**)&w->poffs_rows, sizeof(int) * kPlaneEnt * n);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&w->poffs_33, sizeof(int) * kPlaneEnt * n);
-        if (e == cudaSuccess) {
-            const int nb = blocks_for(n, 128);
-            switch (a->g.D) {
-                case 2:
-                    k_plane_lists<2><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 0, w->poffs_rows);
-                    k_plane_lists<2><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 1, w->poffs_33);
-                    break;
-                case 3:
-                    k_plane_lists<3><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 0, w->poffs_rows);
-                    k_plane_lists<3><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 1, w->poffs_33);
-                    break;
-                default:
-                    k_plane_lists<4><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 0, w->poffs_rows);
-                    k_plane_lists<4><<<nb, 128, 0, st>>>(a->g, a->d_shape, a->nplanes, 1, w->poffs_33);
-                    break;
-            }
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) {
-            cudaFree(w->poffs_rows); cudaFree(w->poffs_33);
-            w->poffs_rows = w->poffs_33 = nullptr;
-            w->relax_blocks = 0;
-            return bfh::cuda_fail(e, "plane lookup lists");
-        }
-    }
     long long warps = w->relax_blocks;
     for (int i = 0; i < 2; ++i)
         if (w->pl_blocks_full[i] > warps) warps = w->pl_blocks_full[i];
@@ -801,7 +760,7 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     out->default_ms = best;
     int tried = 1;
     const bool cls = opts && opts->succ_class;
-    const bool has33 = w->M33 && !cls, hasp = w->poffs_rows && !cls, hast = a->d_tent != nullptr;
+    const bool has33 = w->M33 && !cls, hasp = a->d_poffs[0] && !cls, hast = a->d_tent != nullptr;
     const bool hasd = !cls && ws_tile(a, w, st) == BF_OK;
     // coordinate descent: each dimension's values with the others at the best
     // so far, two rounds

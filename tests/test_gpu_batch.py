@@ -90,3 +90,43 @@ def test_batch_full_size_64_uneven_unicycles():
     for r, s in zip(res, solo):
         assert r["iters"] == s["iters"] and r["status"] == s["status"]
         assert np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"])
+
+
+@pytest.mark.parametrize("sched", [
+    dict(fuse_mark=-1, window33=1, plane_lists=1, templates=1, pair_inputs=1),
+    dict(fuse_mark=1, window33=1, plane_lists=1, templates=1, pair_inputs=0),
+    dict(fuse_mark=0, window33=1, plane_lists=1, templates=0, pair_inputs=1),
+    dict(fuse_mark=0, window33=0, plane_lists=0, templates=1, pair_inputs=0),
+    dict(fuse_mark=1, window33=0, plane_lists=1, templates=0, pair_inputs=1),
+])
+def test_batch_schedules_equal_solo_and_oracle(sched):
+    """The batched form's schedules (3 x 3 window table, plane lookup lists and
+    their kernel, predecessor templates, two inputs per iteration, marking in
+    relax or a propagate launch): every instance equal to its solo solve and
+    the instances on the oracle's boxes equal to the oracle."""
+    ws = [wl.unicycle3d(n=(40, 36, 16), n_obstacles=5, seed=1),
+          wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0))),
+          wl.unicycle3d(n=(70, 64, 24), n_obstacles=12, seed=2, cost_c=0.7),
+          wl.di2d(tau=0.3)]
+    obs = [oracle_boxes(w) for w in ws]
+    As = [import_boxes(w, ob) for w, ob in zip(ws, obs)]
+    for A in As:
+        bf.bf_set_batch_schedule(A, **sched)
+    res = bf.bf_solve_batch(As, [w.G for w in ws], targets=[w.target for w in ws],
+                            avoids=[w.avoid for w in ws])
+    for r, w, ob in zip(res, ws, obs):
+        ref = oracle.solve(w.grid.n, w.grid.periodic, ob, w.G, w.terminal(), w.avoid)
+        assert r["iters"] == ref["iters"] and r["status"] == ref["status"]
+        assert np.array_equal(r["V"], ref["V"]) and np.array_equal(r["mu"], ref["mu"])
+
+
+def test_batch_tuner_keeps_results():
+    ws = [wl.unicycle3d(n=(40, 36, 16), n_obstacles=5, seed=1 + i) for i in range(4)]
+    As = [bf.abs_build_workload(w) for w in ws]
+    solo = [bf.bf_solve(A, w.G, target=w.target, avoid=w.avoid) for A, w in zip(As, ws)]
+    t = bf.bf_tune_batch(As, [w.G for w in ws], targets=[w.target for w in ws], avoids=[w.avoid for w in ws])
+    assert t["candidates"] >= 6 and t["best_ms"] <= t["default_ms"]
+    assert t["fuse_mark"] in (-1, 0, 1)
+    res = bf.bf_solve_batch(As, [w.G for w in ws], targets=[w.target for w in ws], avoids=[w.avoid for w in ws])
+    for r, s in zip(res, solo):
+        assert r["iters"] == s["iters"] and np.array_equal(r["V"], s["V"]) and np.array_equal(r["mu"], s["mu"])
