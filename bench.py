@@ -259,6 +259,8 @@ def ours(args, rank, world, local_rank):
         desc = desc.replace("stored boxes", "hybrid mode: %d of %d inputs stored" % (A.stored_inputs, U))
     if args.schedule == "inplace":
         desc += ", in-place passes (value = Jacobi canonical relaxations / time)"
+    if args.frontier_cache and A.mode != bf.MODE_STORED:
+        desc += ", frontier cache of %d cells" % args.frontier_cache
 
     G = torch.from_numpy(w.G).to(dev)
     tg = torch.from_numpy(w.target).to(dev)
@@ -271,6 +273,7 @@ def ours(args, rank, world, local_rank):
     def solve(**kw):
         kw.setdefault("host_loop", args.host_loop)
         kw.setdefault("schedule", sched)
+        kw.setdefault("frontier_cache", args.frontier_cache)
         return bf.bf_solve(A, G, target=tg, avoid=av, V=V, mu=mu, stream=stream, **kw)
 
     # pass schedule picked by timing (slice target, marking, relax grid); results do not depend on it
@@ -754,6 +757,9 @@ def main():
                     help="pass schedule of the timed solves (the canonical count is always Jacobi's)")
     ap.add_argument("--hybrid-inputs", type=int, default=None,
                     help="memory-regulated build storing the box records of this many inputs")
+    ap.add_argument("--frontier-cache", type=int, default=0,
+                    help="recompute / hybrid builds: cells of each pass's frontier whose regenerated records "
+                         "are kept for the next pass")
     ap.add_argument("--recompute", action="store_true",
                     help="build the abstraction in recompute mode (boxes regenerated inside relax)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -145,8 +145,10 @@ BF_API int abs_build(const bf_dynamics *dyn, const bf_grid *grid, const bf_input
  * in box_budget bytes; the boxes of the other inputs are regenerated inside
  * the relaxation kernel.  K = U gives a stored-mode abstraction, K = 0 (or a
  * system whose boxes do not fit the compact records) a recompute-mode one;
- * otherwise the mode is BF_MODE_HYBRID.  Boxes, and so every result, are
- * bit-identical to the other modes.  The predecessor index and the inputs
+ * otherwise the mode is BF_MODE_HYBRID.  (The transitions of the other
+ * inputs that the next round needs can be kept per solve: the frontier cache
+ * of bf_solve_opts.)  Boxes, and so every result, are bit-identical to the
+ * other modes.  The predecessor index and the inputs
  * are not counted in box_budget.  Errors: as abs_build, and BF_ERR_INVALID
  * for a negative budget. */
 BF_API int abs_build_hybrid(const bf_dynamics *dyn, const bf_grid *grid, const bf_inputs *inputs,
@@ -253,6 +255,15 @@ typedef struct {
      * follows G's layout and rules ([C][U] double). */
     const uint8_t *succ_class; /* [C]                                           */
     const double *G_class;     /* [C][U]                                        */
+    /* Frontier cache (Sec. IV-B memory regulation: after each round keep only
+     * the transitions the next round needs), for abstractions whose boxes are
+     * regenerated (recompute mode, or the inputs a hybrid abstraction does not
+     * store): the regenerated records of the first frontier_cache cells of each
+     * pass's frontier are kept for the next pass, where the cells still in the
+     * frontier read them instead of regenerating them; the others are dropped.
+     * Device memory in the handle's workspace: 8 C + 16 (U - K) frontier_cache
+     * bytes.  0: no cache (stored-mode abstractions never use one). */
+    int64_t frontier_cache;
 } bf_solve_opts;
 
 /* bf_solve -- Algorithm 1 (Sec. IV-A) on the abstraction with running cost G

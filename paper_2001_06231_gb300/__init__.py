@@ -70,7 +70,8 @@ class SolveStats(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int64), ("schedule", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("terminal", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
-                ("stats", ctypes.c_void_p), ("succ_class", ctypes.c_void_p), ("G_class", ctypes.c_void_p)]
+                ("stats", ctypes.c_void_p), ("succ_class", ctypes.c_void_p), ("G_class", ctypes.c_void_p),
+                ("frontier_cache", ctypes.c_int64)]
 
 
 class TuneResult(ctypes.Structure):
@@ -285,11 +286,13 @@ def abs_from_boxes(grid, boxes, stream=None):
 
 def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0, schedule=SCHED_AUTO,
              host_loop=False, trace_cap=0, V=None, mu=None, stream=None, count_exact=False,
-             time_kernels=False, succ_class=None, G_class=None):
+             time_kernels=False, succ_class=None, G_class=None, frontier_cache=0):
     """Algorithm 1 on the device.  Returns dict(V, mu, iters, status, stats[, trace]).
 
     succ_class ([C] mask) with G_class ([C][U]): running cost G_class(x,u) for
-    successors in the class, G(x,u) for the others.
+    successors in the class, G(x,u) for the others.  frontier_cache: cells of
+    each pass's frontier whose regenerated box records are kept for the next
+    pass (recompute and hybrid abstractions).
     """
     C = abstraction.ncells
     Gc = _host(G, np.float64)
@@ -310,6 +313,7 @@ def bf_solve(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0
     opts.terminal = _ptr(tm)
     opts.succ_class = _ptr(rc_mask)
     opts.G_class = _ptr(rc_cost)
+    opts.frontier_cache = int(frontier_cache)
     stats = SolveStats()
     opts.stats = ctypes.addressof(stats)
     trace = None

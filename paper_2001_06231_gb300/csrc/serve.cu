@@ -13,6 +13,11 @@
 //   3. reads the per-request counters, copies the results of finished
 //      requests to their host buffers and frees their state.
 // Requests that arrive while others are on the GPU thus join the next step.
+// A request that finds the engine idle and no other request waiting runs at
+// once as a plain bf_solve on the stream (one graph launch for all its passes,
+// on the abstraction's cached workspace, whose bytes count against the budget
+// from the first such request on); requests arriving meanwhile queue and go
+// to the engine together.
 // The engine runs each request exactly as bf_solve would, so results do not
 // depend on what else is in the mix.
 #include <algorithm>
@@ -23,9 +28,12 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "batch_engine.cuh"
+
+size_t solve_ws_bytes(const bf_abstraction* a);   // solve.cu
 
 namespace {
 
@@ -94,6 +102,7 @@ struct bf_server {
     std::vector<Cached> cache;
     uint64_t next_id = 1;
     bool stop = false;
+    std::unordered_set<const bf_abstraction*> direct;   // abstractions whose bf_solve workspace is counted
     std::thread th;
     bfb::Engine* eng = nullptr;
 };
@@ -142,6 +151,7 @@ const bf_abstraction* resolve(bf_server* s, Req* r, std::unique_lock<std::mutex>
         const size_t K = std::min<size_t>((size_t)r->sys.ninputs, box_budget / per_input);
         mode = K > 0 ? BF_MODE_HYBRID : BF_MODE_RECOMPUTE;
         est = base + K * per_input;
+        box_budget = K * per_input;          // the stored records only (no frontier cache)
     }
     if (mode < 0) {
         // fits once other requests leave, unless nothing is running
@@ -180,9 +190,52 @@ void engine_loop(bf_server* s) {
         std::vector<std::pair<Req*, const bf_abstraction*>> admit;
         std::vector<Req*> failed;
         bool waiting = false;               // requests left in the queue after admission
+        Req* solo = nullptr;                // a lone request on an idle engine: plain bf_solve
+        const bf_abstraction* solo_a = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->m);
             s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
+            if (s->stop && s->pending.empty() && s->active.empty()) break;
+            if (s->active.empty() && s->pending.size() == 1) {
+                Req* r = s->pending.front();
+                bool wait = false;
+                const bf_abstraction* a = resolve(s, r, lk, &wait);
+                if (a) {
+                    const size_t ws = s->direct.count(a) ? 0 : solve_ws_bytes(a);
+                    if (s->used + ws <= s->budget && s->pending.size() == 1 && s->pending.front() == r) {
+                        s->pending.pop_front();
+                        if (ws) {
+                            s->direct.insert(a);
+                            s->used += ws;
+                        }
+                        solo = r;
+                        solo_a = a;
+                        r->res.mode = a->mode;
+                        r->res.admit_s = now_s();
+                    }
+                }
+            }
+        }
+        if (solo) {
+            bf_solve_opts o;
+            memset(&o, 0, sizeof o);
+            o.terminal = solo->pT;
+            o.max_iters = solo->max_iters;
+            int64_t it = 0;
+            int32_t stt = 0;
+            const int rc = bf_solve(solo_a, solo->pG, solo->pT ? nullptr : solo->pTg, solo->pAv, &o, solo->V,
+                                    solo->mu, &it, &stt, s->st);
+            std::lock_guard<std::mutex> lk(s->m);
+            solo->res.iters = it;
+            solo->res.status = stt;
+            solo->res.error = rc;
+            solo->res.finish_s = now_s();
+            solo->res.done = 1;
+            s->cv_done.notify_all();
+            continue;
+        }
+        {
+            std::unique_lock<std::mutex> lk(s->m);
             if (s->stop && s->pending.empty() && s->active.empty()) break;
             while (!s->pending.empty() && (int)(s->active.size() + admit.size()) < s->max_active) {
                 Req* r = s->pending.front();

@@ -77,6 +77,10 @@ struct bf_solve_ws {
     TileState* tile = nullptr;      // tile geometry and tensor maps (set up on first use)
     bool tile_failed = false;       // the abstraction does not fit the tile form
     unsigned* f1bits = nullptr;     // [S] F1 as a bitmap (tile relax)
+    unsigned long long* fc[2] = {nullptr, nullptr};   // frontier cache buffers [U - K][fc_alloc]
+    long long* fc_tag = nullptr;                      // [C]
+    long long fc_alloc = 0;         // cells the buffers hold
+    long long fc_cap = 0;           // cells the current solve caches (0: none)
     int slice_target = kSliceTarget;
     bool tuned = false;             // bf_tune chose the schedule below
     bool fuse_mark = true;          // relax marks F2 (no propagate launch per pass)
@@ -105,6 +109,7 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->rmask); cudaFree(w->GRint); cudaFree(w->VN); cudaFree(w->VR); cudaFree(w->M2R);
     cudaFree(w->M3R); cudaFree(w->stage_GR);
     cudaFree(w->f1bits);
+    cudaFree(w->fc[0]); cudaFree(w->fc[1]); cudaFree(w->fc_tag);
     if (w->tile) tile_free(w->tile);
     delete w;
 }
@@ -231,6 +236,17 @@ static int full_wave(K kernel, int threads) {
     return per_sm * sm_count();
 }
 
+// Device bytes a bf_solve workspace of this abstraction holds at most: state,
+// window tables, costs, staging of host inputs and outputs, slice buffers
+// (one wave of 8 warps per block on every SM, at most 8 blocks per SM) and
+// the F1 bitmap of the tile relax.
+size_t solve_ws_bytes(const bf_abstraction* a) {
+    const size_t C = (size_t)a->g.C, U = (size_t)a->g.U, S = (C + 31) / 32;
+    const size_t slice = 2ull * kSliceTargetMax * (size_t)sm_count() * 8 * 8 * 32;
+    return C * (5 * 8 + 1 + 4 + 4) + 4 * S + 2 * 8 * C * U + 8 * C + 8 * C + 2 * C + slice * 12 + slice / 8 + 4 * S +
+           sizeof(Counters);
+}
+
 static int ws_get(const bf_abstraction* a, bf_solve_ws** out) {
     bf_abstraction* am = const_cast<bf_abstraction*>(a);
     if (am->ws) { *out = am->ws; return BF_OK; }
@@ -274,6 +290,12 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     if (w->use_tmpl && a->d_tent) {
         v.tptr = a->d_tptr;
         v.tent = a->d_tent;
+    }
+    if (w->fc_cap > 0) {
+        v.fc[0] = w->fc[0];
+        v.fc[1] = w->fc[1];
+        v.fc_tag = w->fc_tag;
+        v.fc_cap = w->fc_cap;
     }
     if (w->dense_pct > 0 && w->tile && !w->cls) {
         v.f1bits = w->f1bits;
@@ -530,6 +552,29 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
         BF_CUDA(cudaMalloc((void**)&w->M2R, 8 * C));
         BF_CUDA(cudaMalloc((void**)&w->M3R, 8 * C));
     }
+    // frontier cache of the regenerated records (recompute / hybrid modes);
+    // the graph holds the view by value: rebuild it when the size changes
+    {
+        long long want = (opts && opts->frontier_cache > 0 && a->nstored < U &&
+                          (a->box_fmt == kBoxRecompute || a->box_fmt == kBoxHybrid))
+                             ? (opts->frontier_cache < C ? opts->frontier_cache : C) : 0;
+        if (want < 0) want = 0;
+        if (want > w->fc_alloc) {
+            cudaFree(w->fc[0]); cudaFree(w->fc[1]);
+            w->fc[0] = w->fc[1] = nullptr;
+            w->fc_alloc = 0;
+            const size_t n = (size_t)want * (size_t)(U - a->nstored);
+            BF_CUDA(cudaMalloc((void**)&w->fc[0], 8 * n));
+            BF_CUDA(cudaMalloc((void**)&w->fc[1], 8 * n));
+            if (!w->fc_tag) BF_CUDA(cudaMalloc((void**)&w->fc_tag, 8 * C));
+            w->fc_alloc = want;
+        }
+        if (want != w->fc_cap) {
+            w->fc_cap = want;
+            if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+            if (w->graph) { cudaGraphDestroy(w->graph); w->graph = nullptr; }
+        }
+    }
     // trace buffer (device side), sized to the request
     const long long tcap = (opts && opts->trace) ? opts->trace_cap : 0;
     if (tcap > w->trace_cap) {
@@ -558,6 +603,7 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     // set-up: lines 1-10 of Algorithm 1
     k_init_counters<<<1, 1, 0, st>>>(w->ctr, cap);
     BF_CUDA(cudaMemsetAsync(w->fbits, 0, 4 * w->nwords, st));
+    if (w->fc_cap > 0) BF_CUDA(cudaMemsetAsync(w->fc_tag, 0, 8 * C, st));    // no cell cached before pass 0
     k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dG, (const unsigned char*)dAv,
                                                      w->Gint, w->ctr);
     if (cls) {

@@ -97,6 +97,13 @@ struct InstView {
     long long* trace;           // [trace_cap][4] or NULL
     long long trace_cap;
     int* stamp;                 // [C] pass that last changed the cell (counting mode) or NULL
+    // frontier cache (recompute / hybrid modes): the records of the inputs u >=
+    // nstored of the first fc_cap cells of each pass's frontier list, in two
+    // buffers [U - nstored][fc_cap] used by alternate passes, and per cell a tag
+    // ((pass + 2) << 32 | position) of the pass and place that wrote them
+    unsigned long long* fc[2];
+    long long* fc_tag;          // [C]
+    long long fc_cap;           // 0: no cache
     unsigned* f1bits;           // [S] the current frontier F1 as a bitmap (tile relax) or NULL
     long long dense_min;        // passes with at least this many F1 cells take the tile relax
                                 // (the list relax returns at once), else the list relax
@@ -777,11 +784,21 @@ __device__ __forceinline__ int wrap_key(const GridDesc& g, const int* k) {
     return key;
 }
 
+// A lane's place in the frontier cache: hit = its cell's records of the
+// previous pass are at old_pos of the old buffer; pos = where this pass keeps
+// them (pos >= fc_cap: not kept).
+struct FcLane {
+    bool hit;
+    long long old_pos;
+    long long pos;
+};
+constexpr unsigned long long kNoRecord = ~0ull;   // a box the compact record cannot hold
+
 // k: the cell's coordinates (only read for wrapping boxes and non-compact
 // formats).
 template <int D, int FMT>
 __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const int* k, int u, bool act,
-                                           PairShape<D>& s) {
+                                           PairShape<D>& s, const FcLane* fl = nullptr) {
     const GridDesc& g = v.g;
     s.valid = false;
     s.slow = false;
@@ -789,9 +806,21 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
     s.sig = 0;
     s.wkey = 0;
     if (!act) return;
-    if (FMT == kBoxCompact || (FMT == kBoxHybrid && u < v.nstored)) {
-        const unsigned long long r =
-            (unsigned long long)__ldcs(reinterpret_cast<const compact_t<D>*>(v.boxes) + (long long)u * g.C + c);
+    bool from_cache = false;
+    unsigned long long r = 0;
+    if constexpr (FMT == kBoxRecompute || FMT == kBoxHybrid) {
+        if (fl && u >= v.nstored) {
+            const long long slot = (long long)(u - v.nstored) * v.fc_cap;
+            if (fl->hit) {
+                r = v.fc[(v.ctr->round + 1) & 1][slot + fl->old_pos];
+                from_cache = r != kNoRecord;
+            }
+            if (from_cache && fl->pos < v.fc_cap) v.fc[v.ctr->round & 1][slot + fl->pos] = r;   // carried over
+        }
+    }
+    if (FMT == kBoxCompact || (FMT == kBoxHybrid && u < v.nstored) || from_cache) {
+        if (!from_cache)
+            r = (unsigned long long)__ldcs(reinterpret_cast<const compact_t<D>*>(v.boxes) + (long long)u * g.C + c);
         const int f0 = rec_byte(r, 1);
         if ((f0 & 0x7F) == 0) return;                 // blocked
         s.valid = true;
@@ -815,7 +844,12 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
         } else {
             b = load_box<D>(v.boxes, (long long)u * g.C + c);
         }
-        if (b.lo[0] == kBlocked) return;
+        if (b.lo[0] == kBlocked) {
+            if constexpr (FMT == kBoxRecompute || FMT == kBoxHybrid)
+                if (fl && u >= v.nstored && fl->pos < v.fc_cap)
+                    v.fc[v.ctr->round & 1][(long long)(u - v.nstored) * v.fc_cap + fl->pos] = 0ull;
+            return;
+        }
         s.valid = true;
         s.have_box = true;
         s.b = b;
@@ -845,6 +879,9 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
         }
         s.sig = rec;
         s.slow = bad;
+        if constexpr (FMT == kBoxRecompute || FMT == kBoxHybrid)
+            if (fl && u >= v.nstored && fl->pos < v.fc_cap)
+                v.fc[v.ctr->round & 1][(long long)(u - v.nstored) * v.fc_cap + fl->pos] = bad ? kNoRecord : rec;
     }
 }
 
@@ -854,14 +891,15 @@ __device__ __forceinline__ void pair_shape(const InstView& v, long long c, const
 // cell changed in the previous pass.
 template <int D, int FMT, bool COUNT, bool CLS = false>
 __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, bool act, int u0, int u1,
-                                             long long round, long long& best, int& bu, bool& in_exact) {
+                                             long long round, long long& best, int& bu, bool& in_exact,
+                                             const FcLane* fl = nullptr) {
     const int lane = threadIdx.x & 31;
     const GridDesc& g = v.g;
     int k[4] = {0, 0, 0, 0};
     if (FMT != kBoxCompact || (g.periodic[0] | g.periodic[1] | g.periodic[2] | g.periodic[3])) cell_coords(g, c, k);
     // the next input's record and cost are loaded while this one is gathered
     PairShape<D> nx;
-    pair_shape<D, FMT>(v, c, k, u0, act, nx);
+    pair_shape<D, FMT>(v, c, k, u0, act, nx, fl);
     double ngv = nx.valid ? __ldcs(v.Gint + (long long)u0 * g.C + c) : 0.0;
     double ngr = 0.0;
     if constexpr (CLS) ngr = nx.valid ? __ldcs(v.GRint + (long long)u0 * g.C + c) : 0.0;
@@ -870,7 +908,7 @@ __device__ __forceinline__ void relax_inputs(const InstView& v, long long c, boo
         const double gv = ngv;
         const double gr = ngr;
         if (u + 1 < u1) {
-            pair_shape<D, FMT>(v, c, k, u + 1, act, nx);
+            pair_shape<D, FMT>(v, c, k, u + 1, act, nx, fl);
             ngv = nx.valid ? __ldcs(v.Gint + (long long)(u + 1) * g.C + c) : 0.0;
             if constexpr (CLS) ngr = nx.valid ? __ldcs(v.GRint + (long long)(u + 1) * g.C + c) : 0.0;
         }
@@ -1160,6 +1198,20 @@ __device__ __forceinline__ void commit_cell(const InstView& v, long long c, long
     if constexpr (MARK) mark_changed<D>(v, changed ? (int)c : -1, changed);
 }
 
+// The frontier-cache place of a lane's cell at frontier position pos.
+__device__ __forceinline__ FcLane fc_lane(const InstView& v, long long c, bool act, long long pos, long long round) {
+    FcLane f;
+    f.pos = act ? pos : v.fc_cap;
+    f.hit = false;
+    f.old_pos = 0;
+    if (act) {
+        const long long t = v.fc_tag[c];
+        f.hit = (t >> 32) == round + 1 && (t & 0xFFFFFFFFll) < v.fc_cap;
+        f.old_pos = t & 0xFFFFFFFFll;
+    }
+    return f;
+}
+
 // Relax cells[first + lane] for lane < count (count <= 32) over all inputs.
 // Returns the number of cells relaxed; in counting mode adds the cells of the
 // exact F1 (some box holds a cell changed in the previous pass) to *exact.
@@ -1173,8 +1225,15 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
     long long best = act ? v.Vkey[c] : 0;
     int bu = -1;
     bool in_exact = false;
-    if constexpr (PLANE != 0) relax_plane<D, COUNT, PLANE == 2>(v, c, act, 0, v.g.U, round, best, bu, in_exact, *st);
-    else relax_inputs<D, FMT, COUNT, CLS>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
+    if constexpr (PLANE != 0) {
+        relax_plane<D, COUNT, PLANE == 2>(v, c, act, 0, v.g.U, round, best, bu, in_exact, *st);
+    } else if ((FMT == kBoxRecompute || FMT == kBoxHybrid) && v.fc_cap > 0) {
+        FcLane fl = fc_lane(v, c, act, first + lane, round);
+        relax_inputs<D, FMT, COUNT, CLS>(v, c, act, 0, v.g.U, round, best, bu, in_exact, &fl);
+        if (act && fl.pos < v.fc_cap) v.fc_tag[c] = ((round + 2) << 32) | fl.pos;
+    } else {
+        relax_inputs<D, FMT, COUNT, CLS>(v, c, act, 0, v.g.U, round, best, bu, in_exact);
+    }
     commit_cell<D, COUNT, MARK>(v, c, best, bu, in_exact, exact);
     return count < 32 ? count : 32;
 }
@@ -1198,8 +1257,16 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
     bool in_exact = false;
     const int u0 = sl * q;
     const int u1 = min(v.g.U, u0 + q);
-    if constexpr (PLANE != 0) relax_plane<D, COUNT, PLANE == 2>(v, c, act, u0, u1, round, best, bu, in_exact, *st);
-    else relax_inputs<D, FMT, COUNT, CLS>(v, c, act, u0, u1, round, best, bu, in_exact);
+    FcLane fl;
+    const bool fc = (FMT == kBoxRecompute || FMT == kBoxHybrid) && v.fc_cap > 0;
+    if constexpr (PLANE != 0) {
+        relax_plane<D, COUNT, PLANE == 2>(v, c, act, u0, u1, round, best, bu, in_exact, *st);
+    } else if (fc) {
+        fl = fc_lane(v, c, act, first + lane, round);
+        relax_inputs<D, FMT, COUNT, CLS>(v, c, act, u0, u1, round, best, bu, in_exact, &fl);
+    } else {
+        relax_inputs<D, FMT, COUNT, CLS>(v, c, act, u0, u1, round, best, bu, in_exact);
+    }
     const long long base = (long long)ch * S * 32 + lane;
     v.cand_key[base + (long long)sl * 32] = best;
     v.cand_u[base + (long long)sl * 32] = (bu < 0 ? 0xFFFF : bu) | (in_exact ? 1 << 16 : 0);
@@ -1221,6 +1288,8 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
         if (bb < 0 || ck < b) { b = ck; bb = cu & 0xFFFF; }
     }
     if (lane == 0) v.slice_cnt[ch] = 0;
+    // every slice has read this cell's tag: the completing warp writes the new one
+    if (fc && act && first + lane < v.fc_cap) v.fc_tag[c] = ((round + 2) << 32) | (first + lane);
     commit_cell<D, COUNT, MARK>(v, c, act ? b : 0, act ? bb : -1, act && ex, exact);
     return count < 32 ? count : 32;
 }

@@ -130,3 +130,23 @@ def test_small_budget_builds_hybrid_or_recompute_mode_and_rejects_oversized():
     r = srv.poll(rid, wait=True)
     assert r["done"] == 1 and r["error"] == -2                      # BF_ERR_OOM
     srv.close()
+
+
+def test_lone_requests_on_an_idle_server():
+    """A request that finds the server idle runs at once as a plain solve (one
+    graph launch); one at a time, then a burst that goes through the batched
+    engine: every result equal to the oracle's on the same boxes."""
+    base = [wl.di2d(tau=0.3), wl.unicycle3d(n=(60, 56, 24), n_obstacles=8),
+            wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0)))]
+    own = [bf.abs_build_workload(w).export_boxes() for w in base]
+    srv = bf.Server(hbm_budget=8 << 30, max_active=8, passes_per_step=4)
+    for w, ob in zip(base, own):                       # one at a time: the idle path
+        r = srv.poll(srv.submit(w.G, target=w.target, avoid=w.avoid, system=system_of(w)), wait=True)
+        assert r["done"] == 1 and r["error"] == 0
+        assert same_result(r, oracle_of(w, ob, w.G, w.target))
+    ids = [srv.submit(w.G * 1.5, target=w.target, avoid=w.avoid, system=system_of(w)) for w in base * 2]
+    res = [srv.poll(i, wait=True) for i in ids]
+    srv.close()
+    for r, w, ob in zip(res, base * 2, own * 2):
+        assert r["done"] == 1 and r["error"] == 0
+        assert same_result(r, oracle_of(w, ob, w.G * 1.5, w.target))
