@@ -41,7 +41,7 @@ UNIT = "relaxations/s"
 PROFILES = {"unicycle3d": os.path.join(ROOT, "profiles", "k_relax_unicycle3d_200x200x64.txt"),
             "fire4d": os.path.join(ROOT, "profiles", "k_relax_fire4d_100x100x36x8.txt")}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2001_06231_gb300", "csrc", f)
-                  for f in ("solve_core.cuh", "solve.cu", "bf_internal.cuh", "dynamics.cuh")]
+                  for f in ("solve_core.cuh", "solve.cu", "solve_plane.cu", "bf_internal.cuh", "dynamics.cuh")]
 FIRE_TARGET_WIDE = ((50.0, 250.0), (50.0, 150.0), (-0.5235987755982988, 0.5235987755982988), (10.0, 15.0))
 
 

@@ -299,7 +299,7 @@ BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *t
  * from which frontier size (share of the cells) a pass relaxes by tiles
  * staged in shared memory (dense_pct; abstractions with a plane shape table
  * and an even dim 0 of at most 256 cells).  Each
- * candidate is solved three times on the given inputs (G, target, avoid and the
+ * candidate is solved five times (one warm, four timed) on the given inputs (G, target, avoid and the
  * optional terminal / succ_class / G_class / max_iters of opts; flags, trace
  * and stats are ignored); the fastest stays in force for later bf_solve calls
  * on the handle.  Results never depend on the schedule.  Errors: as bf_solve. */

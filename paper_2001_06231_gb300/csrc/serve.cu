@@ -13,11 +13,11 @@
 //   3. reads the per-request counters, copies the results of finished
 //      requests to their host buffers and frees their state.
 // Requests that arrive while others are on the GPU thus join the next step.
-// A request that finds the engine idle and no other request waiting runs at
-// once as a plain bf_solve on the stream (one graph launch for all its passes,
-// on the abstraction's cached workspace, whose bytes count against the budget
-// from the first such request on); requests arriving meanwhile queue and go
-// to the engine together.
+// While the engine is idle and at most kDirectMax requests wait, the oldest
+// runs at once as a plain bf_solve on the stream (one graph launch for all
+// its passes, on the abstraction's cached workspace, whose bytes count against
+// the budget from the first such request on); a longer queue goes to the
+// engine together.
 // The engine runs each request exactly as bf_solve would, so results do not
 // depend on what else is in the mix.
 #include <algorithm>
@@ -36,6 +36,10 @@
 size_t solve_ws_bytes(const bf_abstraction* a);   // solve.cu
 
 namespace {
+
+// An idle engine takes up to this many waiting requests one at a time as plain
+// solves (one graph launch each); a longer queue goes to the batched engine.
+constexpr int kDirectMax = 4;
 
 double now_s() {
     using namespace std::chrono;
@@ -196,13 +200,14 @@ void engine_loop(bf_server* s) {
             std::unique_lock<std::mutex> lk(s->m);
             s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
             if (s->stop && s->pending.empty() && s->active.empty()) break;
-            if (s->active.empty() && s->pending.size() == 1) {
+            if (s->active.empty() && !s->pending.empty() && s->pending.size() <= (size_t)kDirectMax) {
                 Req* r = s->pending.front();
                 bool wait = false;
                 const bf_abstraction* a = resolve(s, r, lk, &wait);
                 if (a) {
                     const size_t ws = s->direct.count(a) ? 0 : solve_ws_bytes(a);
-                    if (s->used + ws <= s->budget && s->pending.size() == 1 && s->pending.front() == r) {
+                    if (s->used + ws <= s->budget && s->pending.size() <= (size_t)kDirectMax &&
+                        s->pending.front() == r) {
                         s->pending.pop_front();
                         if (ws) {
                             s->direct.insert(a);

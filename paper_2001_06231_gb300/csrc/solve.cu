@@ -696,7 +696,7 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
 // schedule tuning
 // ---------------------------------------------------------------------------
 
-// Time one configuration: one warm solve, then the mean of two.
+// Time one configuration: one warm solve, then the mean of four.
 static int tune_time(const bf_abstraction* a, const double* G, const uint8_t* target, const uint8_t* avoid,
                      const bf_solve_opts* o, double* V, uint8_t* mu, cudaStream_t st, double* ms) {
     int64_t iters;
@@ -707,14 +707,14 @@ static int tune_time(const bf_abstraction* a, const double* G, const uint8_t* ta
     BF_CUDA(cudaEventCreate(&e0));
     BF_CUDA(cudaEventCreate(&e1));
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 2 && rc == BF_OK; ++r) rc = bf_solve(a, G, target, avoid, o, V, mu, &iters, &status, st);
+    for (int r = 0; r < 4 && rc == BF_OK; ++r) rc = bf_solve(a, G, target, avoid, o, V, mu, &iters, &status, st);
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     float t = 0.f;
     cudaEventElapsedTime(&t, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    *ms = t / 2.0;
+    *ms = t / 4.0;
     return rc;
 }
 

@@ -1120,30 +1120,29 @@ __device__ __forceinline__ void relax_plane(const InstView& v, long long c, bool
             __syncwarp();                                        // before the stage is overwritten
             continue;
         }
-        // records and costs are loaded two pairs ahead of the pair being gathered
-        unsigned long long nr0 = 0ull, nr1 = 0ull, mr0 = 0ull, mr1 = 0ull;
-        double ng0 = 0.0, ng1 = 0.0, mg0 = 0.0, mg1 = 0.0;
+        // the next pair's records and costs are loaded while this pair is gathered
+        unsigned long long nr0 = 0ull, nr1 = 0ull;
+        double ng0 = 0.0, ng1 = 0.0;
         if (grp) {
-            const long long C = g.C;
-            nr0 = (unsigned long long)__ldcs(rp + (long long)u0 * C);
-            ng0 = __ldcs(gp + (long long)u0 * C);
-            if (u0 + 1 < u1) { nr1 = (unsigned long long)__ldcs(rp + (long long)(u0 + 1) * C); ng1 = __ldcs(gp + (long long)(u0 + 1) * C); }
-            if (u0 + 2 < u1) { mr0 = (unsigned long long)__ldcs(rp + (long long)(u0 + 2) * C); mg0 = __ldcs(gp + (long long)(u0 + 2) * C); }
-            if (u0 + 3 < u1) { mr1 = (unsigned long long)__ldcs(rp + (long long)(u0 + 3) * C); mg1 = __ldcs(gp + (long long)(u0 + 3) * C); }
+            nr0 = (unsigned long long)__ldcs(rp + (long long)u0 * g.C);
+            ng0 = __ldcs(gp + (long long)u0 * g.C);
+            if (u0 + 1 < u1) {
+                nr1 = (unsigned long long)__ldcs(rp + (long long)(u0 + 1) * g.C);
+                ng1 = __ldcs(gp + (long long)(u0 + 1) * g.C);
+            }
         }
         for (int u = u0; u < u1; u += 2) {
             const bool two = u + 1 < u1;
             const unsigned long long r0 = nr0, r1 = nr1;
             const double g0 = ng0, g1 = ng1;
-            nr0 = mr0; nr1 = mr1; ng0 = mg0; ng1 = mg1;
             if (grp) {
-                if (u + 4 < u1) {
-                    mr0 = (unsigned long long)__ldcs(rp + (long long)(u + 4) * g.C);
-                    mg0 = __ldcs(gp + (long long)(u + 4) * g.C);
+                if (u + 2 < u1) {
+                    nr0 = (unsigned long long)__ldcs(rp + (long long)(u + 2) * g.C);
+                    ng0 = __ldcs(gp + (long long)(u + 2) * g.C);
                 }
-                if (u + 5 < u1) {
-                    mr1 = (unsigned long long)__ldcs(rp + (long long)(u + 5) * g.C);
-                    mg1 = __ldcs(gp + (long long)(u + 5) * g.C);
+                if (u + 3 < u1) {
+                    nr1 = (unsigned long long)__ldcs(rp + (long long)(u + 3) * g.C);
+                    ng1 = __ldcs(gp + (long long)(u + 3) * g.C);
                 }
             }
             const bool v0 = grp && (rec_byte(r0, 1) & 0x7F) != 0;
