@@ -285,10 +285,12 @@ def ours(args, rank, world, local_rank):
         tp_ = vals[5] if len(vals) > 5 else 1
         pr_ = vals[6] if len(vals) > 6 else 0
         dn_ = vals[7] if len(vals) > 7 else 0
+        oc_ = vals[8] if len(vals) > 8 else 0
         bf.bf_set_schedule(A, slice_target=st_, fuse_mark=fm_, relax_blocks=rb_, window33=w33_, plane_lists=pl_,
-                           templates=tp_, pair_inputs=pr_, dense_pct=dn_, stream=stream)
+                           templates=tp_, pair_inputs=pr_, dense_pct=dn_, occupancy=oc_, stream=stream)
         tuned = {"slice_target": st_, "fuse_mark": fm_, "relax_blocks": rb_, "window33": w33_, "plane_lists": pl_,
-                 "templates": tp_, "pair_inputs": pr_, "dense_pct": dn_, "source": "--set-schedule"}
+                 "templates": tp_, "pair_inputs": pr_, "dense_pct": dn_, "occupancy": oc_,
+                 "source": "--set-schedule"}
     elif not args.no_tune:
         tuned = bf.bf_tune(A, G, target=tg, avoid=av, stream=stream)
     # canonical work (exact F1 of Algorithm 1 with Jacobi passes), counted once on the device
@@ -764,11 +766,12 @@ def main():
                     help="build the abstraction in recompute mode (boxes regenerated inside relax)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default pass schedule (no bf_tune)")
-    ap.add_argument("--set-schedule", default=None, metavar="S,F,B,W[,P[,T[,I[,N]]]]",
+    ap.add_argument("--set-schedule", default=None, metavar="S,F,B,W[,P[,T[,I[,N[,O]]]]]",
                     help="put this pass schedule in force instead of bf_tune: slice target, marking in relax (0/1), "
                          "relax blocks (0: one wave), 3 x 3 window table (0/1), plane lookup lists (0/1, default 1), "
                          "predecessor templates (0/1, default 1), two inputs per relax iteration (0/1, default 0), "
-                         "tile relax from this percentage of the cells in F1 (0: never, default) "
+                         "tile relax from this percentage of the cells in F1 (0: never, default), "
+                         "one block per SM more for the plane relax (0/1, default 0) "
                          "-- reproduces a tuned schedule under a profiler, "
                          "whose timings would sway bf_tune")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -295,7 +295,8 @@ BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *t
  * marked from the planes' predecessor templates (the rows of pred(y) of Eq.
  * (pred) for every cell y of a plane, when every box of a plane and input is
  * the plane's entry) instead of the per-cell bounding boxes of pred, and
- * (with the lookup lists) whether relax takes two inputs per iteration, and
+ * (with the lookup lists) whether relax takes two inputs per iteration and
+ * runs one block per SM more (occupancy), and
  * from which frontier size (share of the cells) a pass relaxes by tiles
  * staged in shared memory (dense_pct; abstractions with a plane shape table
  * and an even dim 0 of at most 256 cells).  Each
@@ -321,6 +322,8 @@ typedef struct {
                                   of the cells relax by tiles: a block per plane
                                   and band of rows, the window-table cells of its
                                   boxes copied to shared memory by TMA; 0: never */
+    int32_t occupancy;         /* 1: the plane relax kernel runs one block per SM
+                                  more than its registers want (some spills)    */
 } bf_tune_result;
 
 BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *target,
@@ -329,8 +332,8 @@ BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *ta
 /* bf_set_schedule -- put a pass schedule in force without timing (a schedule
  * bf_tune printed earlier, or a fixed one): slice_target 0..4, fuse_mark,
  * relax_blocks (<= 0 or above one wave: one wave), window33, plane_lists,
- * templates, pair_inputs and dense_pct (0..100; ignored where the tile form
- * does not apply) of *sched are read, the rest ignored; window33 has no effect on
+ * templates, pair_inputs, occupancy and dense_pct (0..100; ignored where the
+ * tile form does not apply) of *sched are read, the rest ignored; window33 has no effect on
  * 1-D grids or solves with a successor class, plane_lists none on
  * abstractions without a plane shape table or solves with a successor class,
  * templates none on abstractions without templates.  Results never depend on the schedule.  Returns BF_OK,

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbfgpu.so")
 
-SOURCES = ["abs_build.cu", "solve.cu", "solve_plane.cu", "solve_tile.cu", "solve_cls.cu", "solve_cls_count.cu", "batch.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["abs_build.cu", "solve.cu", "solve_stored.cu", "solve_recompute.cu", "solve_hybrid.cu", "solve_plane.cu", "solve_tile.cu", "solve_cls.cu", "solve_cls_count.cu", "batch.cu", "serve.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]

@@ -70,8 +70,10 @@ struct bf_solve_ws {
     cudaGraph_t graph = nullptr;
     int relax_blocks = 0, prop_blocks = 0, compact_blocks = 0;
     int relax_blocks_full = 0;      // one full wave of the relax kernel
-    int pl_blocks_full[2] = {0, 0}; // one full wave of the plane relax kernel (one input / two at a time)
+    int pl_blocks_full[4] = {0, 0, 0, 0};   // one full wave of the plane relax kernel, by form
+                                            // (pair + 2 occ)
     bool pair = false;              // the plane relax kernel takes two inputs per iteration
+    bool occ = false;               // ... with one block per SM more
     int dense_pct = 0;              // passes whose F1 holds at least this share (percent) of the
                                     // cells take the tile relax; 0: never
     TileState* tile = nullptr;      // tile geometry and tensor maps (set up on first use)
@@ -148,14 +150,18 @@ __global__ void k_init_counters(Counters* ctr, long long cap) {
 // ---------------------------------------------------------------------------
 // pass kernels
 // ---------------------------------------------------------------------------
-template <int D, int FMT, bool COUNT, bool MARK>
-__global__ void __launch_bounds__(256, (FMT == kBoxRecompute || FMT == kBoxHybrid) ? 2 : 4) k_relax(InstView v) {
-    relax_pass<D, FMT, COUNT, MARK, false>(v);
-}
+// Generic relax (solve_stored.cu: wide and compact records;
+// solve_recompute.cu, solve_hybrid.cu: the modes that regenerate boxes).
+void launch_relax_stored(const InstView& v, int fmt, bool count, bool mark, int blocks, cudaStream_t st);
+int relax_wave_stored(int D, int fmt);
+void launch_relax_recompute(const InstView& v, bool count, bool mark, int blocks, cudaStream_t st);
+int relax_wave_recompute(int D);
+void launch_relax_hybrid(const InstView& v, bool count, bool mark, int blocks, cudaStream_t st);
+int relax_wave_hybrid(int D);
 
 // Relax on abstractions with plane lookup lists (solve_plane.cu).
-int plane_relax_wave(int D, bool pair);
-void launch_relax_plane(const InstView& v, bool count, bool mark, bool pair, int blocks, cudaStream_t st);
+int plane_relax_wave(int D, bool pair, bool occ);
+void launch_relax_plane(const InstView& v, bool count, bool mark, bool pair, bool occ, int blocks, cudaStream_t st);
 
 // Propagate (warp per changed cell): set F2's bits from the changed list
 // (set-up: the finite cells; the passes mark F2 inside relax).
@@ -339,22 +345,19 @@ struct PassTimers {
 template <int D, int FMT>
 static void launch_relax(bf_solve_ws* w, const InstView& v, cudaStream_t st, bool count) {
     if constexpr (FMT == kBoxCompact && D >= 2) {
-        const int full = w->pl_blocks_full[w->pair && !count ? 1 : 0];
+        const int form = count ? 0 : (w->pair ? 1 : 0) + (w->occ ? 2 : 0);
+        const int full = w->pl_blocks_full[form];
         if (v.poffs && v.g.U <= kPlaneUMax && full > 0) {
             // the same share of its own wave as the generic kernel's grid
             int b = (int)(((long long)w->relax_blocks * full + w->relax_blocks_full - 1) / w->relax_blocks_full);
             if (b < 1) b = 1;
-            launch_relax_plane(v, count, w->fuse_mark, w->pair, b, st);
+            launch_relax_plane(v, count, w->fuse_mark, w->pair, w->occ && !count, b, st);
             return;
         }
     }
-    if (w->fuse_mark) {
-        if (count) k_relax<D, FMT, true, true><<<w->relax_blocks, 256, 0, st>>>(v);
-        else k_relax<D, FMT, false, true><<<w->relax_blocks, 256, 0, st>>>(v);
-    } else {
-        if (count) k_relax<D, FMT, true, false><<<w->relax_blocks, 256, 0, st>>>(v);
-        else k_relax<D, FMT, false, false><<<w->relax_blocks, 256, 0, st>>>(v);
-    }
+    if (FMT == kBoxRecompute) launch_relax_recompute(v, count, w->fuse_mark, w->relax_blocks, st);
+    else if (FMT == kBoxHybrid) launch_relax_hybrid(v, count, w->fuse_mark, w->relax_blocks, st);
+    else launch_relax_stored(v, FMT, count, w->fuse_mark, w->relax_blocks, st);
 }
 
 template <int D>
@@ -404,15 +407,10 @@ static void launch_setup_frontier(const bf_abstraction* a, bf_solve_ws* w, const
 template <int D>
 static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
     if (D >= 2 && a->box_fmt == kBoxCompact && a->d_shape && a->g.U <= kPlaneUMax) {
-        w->pl_blocks_full[0] = plane_relax_wave(D, false);
-        w->pl_blocks_full[1] = plane_relax_wave(D, true);
+        for (int f = 0; f < 4; ++f) w->pl_blocks_full[f] = plane_relax_wave(D, f & 1, f >> 1);
     }
-    switch (a->box_fmt) {
-        case kBoxCompact: w->relax_blocks = full_wave(k_relax<D, kBoxCompact, false, true>, 256); break;
-        case kBoxRecompute: w->relax_blocks = full_wave(k_relax<D, kBoxRecompute, false, true>, 256); break;
-        case kBoxHybrid: w->relax_blocks = full_wave(k_relax<D, kBoxHybrid, false, true>, 256); break;
-        default: w->relax_blocks = full_wave(k_relax<D, kBoxWide, false, true>, 256); break;
-    }
+    w->relax_blocks = a->box_fmt == kBoxRecompute ? relax_wave_recompute(D)
+                      : a->box_fmt == kBoxHybrid ? relax_wave_hybrid(D) : relax_wave_stored(D, a->box_fmt);
     w->prop_blocks = full_wave(k_propagate<D>, 256);
     // marking inside relax pays when predecessor boxes are small: the marks
     // then cost less than a separate launch per pass (bf_tune may override)
@@ -433,7 +431,7 @@ static int ws_blocks(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
     // fewer than 2 x slice_target x warps (chunk, slice) items
     w->relax_blocks_full = w->relax_blocks;
     long long warps = w->relax_blocks;
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (w->pl_blocks_full[i] > warps) warps = w->pl_blocks_full[i];
     warps *= 8;
     const long long cap = 2LL * kSliceTargetMax * warps * 32;
@@ -747,6 +745,7 @@ struct Sched {
     bool plane = true;
     bool tmpl = true;
     bool pair = false;
+    bool occ = false;
     int dense = 0;
 };
 
@@ -761,6 +760,7 @@ static void set_schedule(bf_solve_ws* w, const Sched& s) {
     w->use_plane = s.plane;
     w->use_tmpl = s.tmpl;
     w->pair = s.pair;
+    w->occ = s.occ;
     w->dense_pct = s.dense;
     w->tuned = true;
     if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
@@ -802,6 +802,7 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     b.plane = w->use_plane;
     b.tmpl = w->use_tmpl;
     b.pair = w->pair;
+    b.occ = w->occ;
     b.dense = w->dense_pct;
     out->default_ms = best;
     int tried = 1;
@@ -811,9 +812,10 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     // coordinate descent: each dimension's values with the others at the best
     // so far, two rounds
     for (int round = 0; round < 2 && rc == BF_OK; ++round) {
-        for (int dim = 0; dim < 8 && rc == BF_OK; ++dim) {
+        for (int dim = 0; dim < 9 && rc == BF_OK; ++dim) {
             const int nval = (dim == 0 || dim == 7) ? (dim == 0 ? 4 : 3) : 2;
             if (dim == 7 && !hasd) continue;
+            if (dim == 8 && !(hasp && base_plane_on(b))) continue;
             if ((dim == 3 && !has33) || (dim == 4 && !hasp) || (dim == 5 && !hast)) continue;
             if (dim == 6 && !(hasp && base_plane_on(b))) continue;
             const Sched base = b;                              // timed already
@@ -828,11 +830,12 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
                     case 4: c.plane = k != 0; break;
                     case 5: c.tmpl = k != 0; break;
                     case 6: c.pair = k != 0; break;
-                    default: c.dense = k == 0 ? 0 : (k == 1 ? 15 : 35); break;
+                    case 7: c.dense = k == 0 ? 0 : (k == 1 ? 15 : 35); break;
+                    default: c.occ = k != 0; break;
                 }
                 if (c.slice == base.slice && c.fuse == base.fuse && c.blocks == base.blocks &&
                     c.use33 == base.use33 && c.plane == base.plane && c.tmpl == base.tmpl && c.pair == base.pair &&
-                    c.dense == base.dense)
+                    c.dense == base.dense && c.occ == base.occ)
                     continue;
                 set_schedule(w, c);
                 double ms = 0.0;
@@ -857,6 +860,7 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     out->templates = (b.tmpl && hast) ? 1 : 0;
     out->pair_inputs = (b.pair && b.plane && hasp) ? 1 : 0;
     out->dense_pct = hasd ? b.dense : 0;
+    out->occupancy = (b.occ && b.plane && hasp) ? 1 : 0;
     out->candidates = tried;
     out->best_ms = best;
     return BF_OK;
@@ -890,6 +894,7 @@ extern "C" int bf_set_schedule(const bf_abstraction* a, const bf_tune_result* sc
     c.tmpl = sched->templates != 0;
     c.pair = sched->pair_inputs != 0;
     c.dense = sched->dense_pct;
+    c.occ = sched->occupancy != 0;
     if (c.dense < 0 || c.dense > 100) {
         bfh::set_error("bf_set_schedule: dense_pct %d outside 0..100", c.dense);
         return BF_ERR_INVALID;
