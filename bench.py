@@ -76,8 +76,12 @@ def make_workload(name, rank=0):
     return w, desc
 
 
-def algorithmic_bytes_per_pair(A):
-    """HBM bytes one executed relaxation streams here: its box record + its cost (8 B)."""
+def algorithmic_bytes_per_pair(A, masked=False):
+    """HBM bytes one executed relaxation streams here: its box record + its cost
+    (8 B); with the cell masks its cost and a U-th of the cell's 8-byte mask
+    (records only for the few boxes that are not their plane's entry)."""
+    if masked:
+        return 8 + 8.0 / A.ninputs
     return A.box_record_bytes + 8
 
 
@@ -286,11 +290,15 @@ def ours(args, rank, world, local_rank):
         pr_ = vals[6] if len(vals) > 6 else 0
         dn_ = vals[7] if len(vals) > 7 else 0
         oc_ = vals[8] if len(vals) > 8 else 0
+        cm_ = vals[9] if len(vals) > 9 else 0
+        pz_ = vals[10] if len(vals) > 10 else 0
+        if_ = vals[11] if len(vals) > 11 else 0
         bf.bf_set_schedule(A, slice_target=st_, fuse_mark=fm_, relax_blocks=rb_, window33=w33_, plane_lists=pl_,
-                           templates=tp_, pair_inputs=pr_, dense_pct=dn_, occupancy=oc_, stream=stream)
+                           templates=tp_, pair_inputs=pr_, dense_pct=dn_, occupancy=oc_, cell_masks=cm_,
+                           pair_dim=pz_, input_frontier=if_, stream=stream)
         tuned = {"slice_target": st_, "fuse_mark": fm_, "relax_blocks": rb_, "window33": w33_, "plane_lists": pl_,
-                 "templates": tp_, "pair_inputs": pr_, "dense_pct": dn_, "occupancy": oc_,
-                 "source": "--set-schedule"}
+                 "templates": tp_, "pair_inputs": pr_, "dense_pct": dn_, "occupancy": oc_, "cell_masks": cm_,
+                 "pair_dim": pz_, "input_frontier": if_, "source": "--set-schedule"}
     elif not args.no_tune:
         tuned = bf.bf_tune(A, G, target=tg, avoid=av, stream=stream)
     # canonical work (exact F1 of Algorithm 1 with Jacobi passes), counted once on the device
@@ -359,7 +367,8 @@ def ours(args, rank, world, local_rank):
     cbpp = canonical_bytes_per_pair(w.grid.ndim)
     bytes_per_launch = canonical * cbpp / max(1, passes)
     achieved = bytes_per_launch / (relax_ms_avg / 1e3) / 1e9
-    bpp = algorithmic_bytes_per_pair(A)
+    masked = bool(tuned and tuned.get("cell_masks") and tuned.get("plane_lists"))
+    bpp = algorithmic_bytes_per_pair(A, masked)
     exec_bytes_per_launch = executed * bpp / max(1, passes)
     # ncu DRAM bytes of the profiled relax launch, per executed pair, scaled to
     # this run's mean launch -- only for the kernel sources and relax form captured
@@ -437,8 +446,10 @@ def ours(args, rank, world, local_rank):
                          cbpp, 2 * w.grid.ndim),
                      "executed_bytes_per_launch": exec_bytes_per_launch,
                      "executed_frac": exec_bytes_per_launch / (relax_ms_avg / 1e3) / 1e9 / peak,
-                     "executed_bytes_note": "executed pairs per launch x %d B (box record %d B + G 8 B)" % (
-                         bpp, bpp - 8)},
+                     "executed_bytes_note": ("executed pairs per launch x %.2f B (G 8 B + a %d-th of the "
+                                             "cell's 8-byte input mask)" % (bpp, U)) if masked else
+                                            ("executed pairs per launch x %d B (box record %d B + G 8 B)" % (
+                                                bpp, bpp - 8))},
         "as_stated": as_stated,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -771,12 +782,15 @@ def main():
                     help="build the abstraction in recompute mode (boxes regenerated inside relax)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default pass schedule (no bf_tune)")
-    ap.add_argument("--set-schedule", default=None, metavar="S,F,B,W[,P[,T[,I[,N[,O]]]]]",
+    ap.add_argument("--set-schedule", default=None, metavar="S,F,B,W[,P[,T[,I[,N[,O[,M[,Z[,R]]]]]]]]",
                     help="put this pass schedule in force instead of bf_tune: slice target, marking in relax (0/1), "
                          "relax blocks (0: one wave), 3 x 3 window table (0/1), plane lookup lists (0/1, default 1), "
                          "predecessor templates (0/1, default 1), two inputs per relax iteration (0/1, default 0), "
                          "tile relax from this percentage of the cells in F1 (0: never, default), "
-                         "one block per SM more for the plane relax (0/1, default 0) "
+                         "one block per SM more for the plane relax (0/1, default 0), "
+                         "per-cell input masks (0/1, default 0: four inputs per iteration with I = 1, else two), "
+                         "plane-pair table dim (0: none, default; 2 .. D - 1), "
+                         "per-input frontier (0/1, default 0) "
                          "-- reproduces a tuned schedule under a profiler, "
                          "whose timings would sway bf_tune")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -295,11 +295,15 @@ BF_API int bf_solve(const bf_abstraction *abs, const double *G, const uint8_t *t
  * marked from the planes' predecessor templates (the rows of pred(y) of Eq.
  * (pred) for every cell y of a plane, when every box of a plane and input is
  * the plane's entry) instead of the per-cell bounding boxes of pred, and
- * (with the lookup lists) whether relax takes two inputs per iteration and
- * runs one block per SM more (occupancy), and
+ * (with the lookup lists) whether relax takes two inputs per iteration,
+ * runs one block per SM more (occupancy) and reads the per-cell input masks
+ * (cell_masks), on grids of 3+ dims with the 3 x 3 windows along which dim >= 2
+ * a plane-pair table halves the lookups (pair_dim), whether (with the
+ * templates) the next frontier is kept per input (input_frontier), and
  * from which frontier size (share of the cells) a pass relaxes by tiles
  * staged in shared memory (dense_pct; abstractions with a plane shape table
- * and an even dim 0 of at most 256 cells).  Each
+ * and an even dim 0 of at most 256 cells); two whole schedules of the
+ * pair-queue relax are timed before the descent starts from the best.  Each
  * candidate is solved five times (one warm, four timed) on the given inputs (G, target, avoid and the
  * optional terminal / succ_class / G_class / max_iters of opts; flags, trace
  * and stats are ignored); the fastest stays in force for later bf_solve calls
@@ -324,6 +328,30 @@ typedef struct {
                                   boxes copied to shared memory by TMA; 0: never */
     int32_t occupancy;         /* 1: the plane relax kernel runs one block per SM
                                   more than its registers want (some spills)    */
+    int32_t cell_masks;        /* 1 or 2: with plane lookup lists, relax reads
+                                  one 8-byte word per cell saying which inputs
+                                  have the plane's record (their lists apply)
+                                  and which another (their records are read);
+                                  no record is read for the first kind and no
+                                  cost for blocked pairs.  1: the inputs in
+                                  turn, pair_inputs ? 4 : 2 per iteration; 2:
+                                  the pairs queued over the lanes, input by
+                                  input, pair_inputs ? 2 : 1 per lane and round
+                                  (only the pairs a cell holds cost work)       */
+    int32_t pair_dim;          /* 2 .. D - 1: with the 3 x 3 window table, a
+                                  second table holds the maximum of two of its
+                                  entries one step apart on this dim, and boxes
+                                  spanning 2+ planes on it read that (half the
+                                  lookups along it, more table upkeep per
+                                  changed cell); 0: none                        */
+    int32_t input_frontier;    /* 1: with the predecessor templates, the next
+                                  frontier is kept per input (one bitmap per
+                                  input, marked from per-input templates) and
+                                  relax with cell_masks takes up only the pairs
+                                  (x, u) whose own box holds a cell changed in
+                                  the previous pass: a pair whose box did not
+                                  change cannot lower W(x), so results are the
+                                  same                                          */
 } bf_tune_result;
 
 BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *target,
@@ -332,12 +360,15 @@ BF_API int bf_tune(const bf_abstraction *abs, const double *G, const uint8_t *ta
 /* bf_set_schedule -- put a pass schedule in force without timing (a schedule
  * bf_tune printed earlier, or a fixed one): slice_target 0..4, fuse_mark,
  * relax_blocks (<= 0 or above one wave: one wave), window33, plane_lists,
- * templates, pair_inputs, occupancy and dense_pct (0..100; ignored where the
- * tile form does not apply) of *sched are read, the rest ignored; window33 has no effect on
+ * templates, pair_inputs, occupancy, cell_masks, pair_dim (0 or 2 .. D - 1;
+ * without effect unless window33 and plane_lists are on), input_frontier
+ * (without effect unless templates are on and U <= 32) and dense_pct
+ * (0..100; ignored where the tile form does not apply) of *sched are read, the
+ * rest ignored; window33 has no effect on
  * 1-D grids or solves with a successor class, plane_lists none on
  * abstractions without a plane shape table or solves with a successor class,
  * templates none on abstractions without templates.  Results never depend on the schedule.  Returns BF_OK,
- * BF_ERR_INVALID (NULL argument, slice_target out of range) or BF_ERR_CUDA /
+ * BF_ERR_INVALID (NULL argument, slice_target or pair_dim out of range) or BF_ERR_CUDA /
  * BF_ERR_OOM (the handle's solve workspace could not be set up). */
 BF_API int bf_set_schedule(const bf_abstraction *abs, const bf_tune_result *sched, void *stream);
 

@@ -78,7 +78,8 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("slice_target", ctypes.c_int32), ("fuse_mark", ctypes.c_int32), ("relax_blocks", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
                 ("window33", ctypes.c_int32), ("plane_lists", ctypes.c_int32), ("templates", ctypes.c_int32),
-                ("pair_inputs", ctypes.c_int32), ("dense_pct", ctypes.c_int32), ("occupancy", ctypes.c_int32)]
+                ("pair_inputs", ctypes.c_int32), ("dense_pct", ctypes.c_int32), ("occupancy", ctypes.c_int32),
+                ("cell_masks", ctypes.c_int32), ("pair_dim", ctypes.c_int32), ("input_frontier", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -363,12 +364,13 @@ def bf_tune(abstraction, G, target=None, avoid=None, terminal=None, max_iters=0,
 
 
 def bf_set_schedule(abstraction, slice_target=2, fuse_mark=1, relax_blocks=0, window33=0, plane_lists=1,
-                    templates=1, pair_inputs=0, dense_pct=0, occupancy=0, stream=None):
+                    templates=1, pair_inputs=0, dense_pct=0, occupancy=0, cell_masks=0, pair_dim=0,
+                    input_frontier=0, stream=None):
     """Put a pass schedule in force on this abstraction's solves (no timing)."""
     s = TuneResult()
     s.slice_target, s.fuse_mark, s.relax_blocks, s.window33 = slice_target, fuse_mark, relax_blocks, window33
     s.plane_lists, s.templates, s.pair_inputs, s.dense_pct = plane_lists, templates, pair_inputs, dense_pct
-    s.occupancy = occupancy
+    s.occupancy, s.cell_masks, s.pair_dim, s.input_frontier = occupancy, cell_masks, pair_dim, input_frontier
     _check(lib().bf_set_schedule(abstraction.handle, ctypes.byref(s), _stream(stream)))
 
 

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -264,10 +265,13 @@ __global__ void k_build_compact(DynDesc dd, GridDesc g, const double* __restrict
 // invariant under translation along dims 0 and 1 (the built-in unicycle and
 // fire models, whose right-hand sides do not depend on x and y) every
 // non-blocked pair (x, u) of a plane has the same relative record.  The entry
-// of (plane, input) is picked in two rounds: any non-blocked record (compare
-// and swap into an empty entry), and, where that one is shared by less than
-// half of the pairs, any record that differs from it; the one more pairs
-// share stays.  Records that differ from the entry are counted.
+// of (plane, input) is picked in up to three rounds, each taking the record of
+// the lowest cell not excluded: the first non-blocked record; where that one
+// is shared by less than half of the pairs, the lowest record that differs
+// from it; where neither is, the lowest that differs from both.  The pick
+// more pairs share stays (the earlier one on a tie), so the table does not
+// depend on the order threads run in.  Records that differ from the entry are
+// counted.
 __device__ __forceinline__ long long plane_of(const GridDesc& g, long long x) {
     if (g.D <= 2) return 0;
     return (long long)grid_div(g, 1, grid_div(g, 0, (unsigned)x));
@@ -279,10 +283,13 @@ __device__ __forceinline__ unsigned long long compact_at(const void* compact, lo
                   : reinterpret_cast<const unsigned long long*>(compact)[p];
 }
 
-// skip (or NULL): entries whose first pick is kept; other: records equal to it are not picked
+// Per entry the lowest cell whose pair is non-blocked and whose record is
+// neither ex1's nor ex2's entry (NULL: none), skipping the entries flagged in
+// skip (or NULL); idx starts at all ones.
 template <int D>
-__global__ void k_shape_pick(GridDesc g, const void* __restrict__ compact, unsigned long long* shape,
-                             const unsigned long long* __restrict__ other, const unsigned char* __restrict__ skip) {
+__global__ void k_shape_first(GridDesc g, const void* __restrict__ compact, unsigned* idx,
+                              const unsigned long long* __restrict__ ex1, const unsigned long long* __restrict__ ex2,
+                              const unsigned char* __restrict__ skip) {
     const long long total = g.C * g.U;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
          p += (long long)gridDim.x * blockDim.x) {
@@ -292,10 +299,17 @@ __global__ void k_shape_pick(GridDesc g, const void* __restrict__ compact, unsig
         if (((rec >> 8) & 0x7F) == 0) continue;                // blocked
         const long long e = plane_of(g, x) * g.U + u;
         if (skip && skip[e]) continue;
-        if (other && rec == other[e]) continue;
-        unsigned long long* q = shape + e;
-        if (*((volatile unsigned long long*)q) == 0ull) atomicCAS(q, 0ull, rec);
+        if ((ex1 && rec == ex1[e]) || (ex2 && rec == ex2[e])) continue;
+        if ((unsigned)x < idx[e]) atomicMin(idx + e, (unsigned)x);
     }
+}
+
+// The records at the picked cells (0 where none was picked).
+template <int D>
+__global__ void k_shape_take(GridDesc g, const void* __restrict__ compact, const unsigned* __restrict__ idx,
+                             long long n, unsigned long long* out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        out[e] = idx[e] == 0xFFFFFFFFu ? 0ull : compact_at<D>(compact, (e % g.U) * g.C + idx[e]);
 }
 
 // Per entry the non-blocked pairs (nb, unless NULL) and those whose record is
@@ -329,11 +343,14 @@ __global__ void k_shape_count(GridDesc g, const void* __restrict__ compact, cons
     }
 }
 
-// Keep the second pick where more pairs share it; flag the entries to retry.
-__global__ void k_shape_choose(long long n, unsigned long long* shape, const unsigned long long* __restrict__ second,
-                               const unsigned* __restrict__ hit1, const unsigned* __restrict__ hit2) {
+// Keep the later pick where more pairs share it (its hits into best).
+__global__ void k_shape_choose(long long n, unsigned long long* shape, const unsigned long long* __restrict__ later,
+                               unsigned* best, const unsigned* __restrict__ hit) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        if (second[e] != 0ull && hit2[e] > hit1[e]) shape[e] = second[e];
+        if (later[e] != 0ull && hit[e] > best[e]) {
+            shape[e] = later[e];
+            best[e] = hit[e];
+        }
 }
 
 __global__ void k_shape_retry(long long n, const unsigned* __restrict__ hit, const unsigned* __restrict__ nb,
@@ -345,10 +362,29 @@ __global__ void k_shape_retry(long long n, const unsigned* __restrict__ hit, con
 // Lookup lists of every (plane, input) of the shape table (thread per entry).
 template <int D>
 __global__ void k_plane_lists(GridDesc g, const unsigned long long* __restrict__ shape, long long P, int m33,
-                              int* out) {
+                              int pz, int* out) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < P * g.U;
          e += (long long)gridDim.x * blockDim.x)
-        plane_offsets<D>(g, shape[e], (int)(e / g.U), m33 != 0, out + e * kPlaneEnt);
+        plane_offsets<D>(g, shape[e], (int)(e / g.U), m33 != 0, pz, out + e * kPlaneEnt);
+}
+
+// Cell masks (thread per cell, U <= 32): bit u when the pair (c, u) has a box
+// whose record is its plane's entry, bit 32 + u when it has another record.
+template <int D>
+__global__ void k_cell_masks(GridDesc g, const void* __restrict__ compact, const unsigned long long* __restrict__ shape,
+                             unsigned long long* out) {
+    const compact_t<D>* rec = reinterpret_cast<const compact_t<D>*>(compact);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.C;
+         c += (long long)gridDim.x * blockDim.x) {
+        const long long p = plane_of_cell<D>(g, c);
+        unsigned long long m = 0;
+        for (int u = 0; u < g.U; ++u) {
+            const unsigned long long r = (unsigned long long)rec[(long long)u * g.C + c];
+            if ((rec_byte(r, 1) & 0x7F) == 0) continue;          // no box
+            m |= (r == shape[p * g.U + u]) ? (1ull << u) : (1ull << (32 + u));
+        }
+        out[c] = m;
+    }
 }
 
 template <int D>
@@ -600,38 +636,53 @@ static int build_shapes_t(bf_abstraction* a, cudaStream_t st) {
     unsigned long long* d_bad = nullptr;
     unsigned long long h_bad = 0;
     const long long n = P * g.U;
-    unsigned long long* second = nullptr;
-    unsigned *hit1 = nullptr, *hit2 = nullptr, *nbk = nullptr;
+    unsigned long long *first = nullptr, *second = nullptr, *third = nullptr;
+    unsigned *hit1 = nullptr, *hit2 = nullptr, *nbk = nullptr, *idx = nullptr;
     unsigned char* skip = nullptr;
     BF_CUDA(cudaMalloc((void**)&shape, sizeof(unsigned long long) * n));
     cudaError_t e = cudaMalloc((void**)&d_bad, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&second, sizeof(unsigned long long) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&hit1, sizeof(unsigned) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&first, sizeof(unsigned long long) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&hit1, sizeof(unsigned) * 4 * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&skip, n);
     if (e == cudaSuccess) {
+        second = first + n;
+        third = first + 2 * n;
         hit2 = hit1 + n;
         nbk = hit1 + 2 * n;
-        e = cudaMemsetAsync(shape, 0, sizeof(unsigned long long) * n, st);
+        idx = hit1 + 3 * n;
+        e = cudaMemsetAsync(hit1, 0, sizeof(unsigned) * 3 * n, st);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(second, 0, sizeof(unsigned long long) * n, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hit1, 0, sizeof(unsigned) * 3 * n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) {
         const int nb = grid_blocks(g.C * g.U, 256);
         const int ne = grid_blocks(n, 256);
-        k_shape_pick<D><<<nb, 256, 0, st>>>(g, a->d_boxes, shape, nullptr, nullptr);
-        k_shape_count<D><<<nb, 256, 0, st>>>(g, a->d_boxes, shape, hit1, nbk);
+        auto pick = [&](unsigned long long* out, const unsigned long long* ex1, const unsigned long long* ex2,
+                        const unsigned char* sk) {
+            if (e == cudaSuccess) e = cudaMemsetAsync(idx, 0xFF, sizeof(unsigned) * n, st);
+            k_shape_first<D><<<nb, 256, 0, st>>>(g, a->d_boxes, idx, ex1, ex2, sk);
+            k_shape_take<D><<<ne, 256, 0, st>>>(g, a->d_boxes, idx, n, out);
+        };
+        pick(first, nullptr, nullptr, nullptr);
+        k_shape_count<D><<<nb, 256, 0, st>>>(g, a->d_boxes, first, hit1, nbk);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(shape, first, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, st);
+        // second round where the first pick is shared by less than half of the pairs
         k_shape_retry<<<ne, 256, 0, st>>>(n, hit1, nbk, skip);
-        k_shape_pick<D><<<nb, 256, 0, st>>>(g, a->d_boxes, second, shape, skip);
+        pick(second, first, nullptr, skip);
         k_shape_count<D><<<nb, 256, 0, st>>>(g, a->d_boxes, second, hit2, nullptr);
         k_shape_choose<<<ne, 256, 0, st>>>(n, shape, second, hit1, hit2);
+        // third round where neither is
+        if (e == cudaSuccess) e = cudaMemsetAsync(hit2, 0, sizeof(unsigned) * n, st);
+        k_shape_retry<<<ne, 256, 0, st>>>(n, hit1, nbk, skip);
+        pick(third, first, second, skip);
+        k_shape_count<D><<<nb, 256, 0, st>>>(g, a->d_boxes, third, hit2, nullptr);
+        k_shape_choose<<<ne, 256, 0, st>>>(n, shape, third, hit1, hit2);
         k_shape_check<D><<<nb, 256, 0, st>>>(g, a->d_boxes, shape, d_bad);
-        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof h_bad, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_bad);
-    cudaFree(second);
+    cudaFree(first);
     cudaFree(hit1);
     cudaFree(skip);
     if (e != cudaSuccess) { cudaFree(shape); return bfh::cuda_fail(e, "plane shape table"); }
@@ -639,12 +690,21 @@ static int build_shapes_t(bf_abstraction* a, cudaStream_t st) {
     a->nplanes = P;
     a->shape_mismatch = (long long)h_bad;
     a->bytes += sizeof(unsigned long long) * P * g.U;
-    // the lookup lists of every entry, for gathers without and with the 3 x 3 windows
-    for (int m33 = 0; m33 < 2; ++m33) {
-        BF_CUDA(cudaMalloc((void**)&a->d_poffs[m33], sizeof(int) * kPlaneEnt * n));
-        k_plane_lists<D><<<grid_blocks(n, 128), 128, 0, st>>>(g, shape, P, m33, a->d_poffs[m33]);
+    // the lookup lists of every entry, for gathers without and with the 3 x 3
+    // windows, and with the plane-pair table along dims 2 and 3
+    for (int k = 0; k < 4; ++k) {
+        if (k >= 2 && k >= D) break;
+        BF_CUDA(cudaMalloc((void**)&a->d_poffs[k], sizeof(int) * kPlaneEnt * n));
+        k_plane_lists<D><<<grid_blocks(n, 128), 128, 0, st>>>(g, shape, P, k >= 1 ? 1 : 0, k >= 2 ? k : 0,
+                                                              a->d_poffs[k]);
         BF_CUDA(cudaGetLastError());
         a->bytes += sizeof(int) * kPlaneEnt * n;
+    }
+    if (g.U <= 32) {
+        BF_CUDA(cudaMalloc((void**)&a->d_fmask, sizeof(unsigned long long) * g.C));
+        k_cell_masks<D><<<grid_blocks(g.C, 256), 256, 0, st>>>(g, a->d_boxes, shape, a->d_fmask);
+        BF_CUDA(cudaGetLastError());
+        a->bytes += sizeof(unsigned long long) * g.C;
     }
     return BF_OK;
 }
@@ -657,7 +717,9 @@ static int build_shapes_t(bf_abstraction* a, cudaStream_t st) {
 // with dim-0 offsets -(rel0 + w0 - 1) .. -rel0.  Offsets of one (p, q, d1)
 // from different inputs merge into their bounding range (a superset).  The
 // result holds pred(y) of Eq. (pred) for every y of p; with the blocked pairs
-// it may hold a few more cells, which the algorithm tolerates.
+// it may hold a few more cells, which the algorithm tolerates.  The per-input
+// templates (U <= 32) keep each input's rows apart: the pairs (x, u) with y in
+// box(x, u) exactly, for the per-input frontier.
 static int build_templates(bf_abstraction* a, cudaStream_t st) {
     const GridDesc& g = a->g;
     const long long P = a->nplanes, U = g.U;
@@ -665,7 +727,9 @@ static int build_templates(bf_abstraction* a, cudaStream_t st) {
     BF_CUDA(cudaMemcpyAsync(S.data(), a->d_shape, sizeof(unsigned long long) * P * U, cudaMemcpyDeviceToHost, st));
     BF_CUDA(cudaStreamSynchronize(st));
     const int n2 = g.D >= 3 ? g.n[2] : 1, n3 = g.D >= 4 ? g.n[3] : 1;
+    // merged: (q, d1) -> dim-0 range; per input: (u, q, d1) -> dim-0 range
     std::vector<std::map<std::pair<int, int>, std::pair<int, int>>> tm((size_t)P);
+    std::vector<std::map<std::tuple<int, int, int>, std::pair<int, int>>> tu((size_t)P);
     for (long long q = 0; q < P; ++q) {
         const int k2 = (int)(q % n2), k3 = (int)(q / n2);
         for (long long u = 0; u < U; ++u) {
@@ -684,19 +748,25 @@ static int build_templates(bf_abstraction* a, cudaStream_t st) {
                     int t2 = k2 + rel[2] + j2;
                     if (g.D >= 3 && g.periodic[2]) t2 = ((t2 % n2) + n2) % n2;
                     if (t2 < 0 || t2 >= n2) continue;
-                    auto& m = tm[(size_t)(t2 + (long long)n2 * t3)];
+                    const size_t tp = (size_t)(t2 + (long long)n2 * t3);
+                    auto& m = tm[tp];
+                    auto& mu_ = tu[tp];
                     for (int j1 = 0; j1 < w[1]; ++j1) {
                         const int d1 = -(rel[1] + j1), lo = -(rel[0] + w[0] - 1), hi = -rel[0];
                         auto it = m.find({(int)q, d1});
                         if (it == m.end()) m[{(int)q, d1}] = {lo, hi};
                         else it->second = {std::min(it->second.first, lo), std::max(it->second.second, hi)};
+                        const auto key = std::make_tuple((int)u, (int)q, d1);
+                        auto iu = mu_.find(key);
+                        if (iu == mu_.end()) mu_[key] = {lo, hi};
+                        else iu->second = {std::min(iu->second.first, lo), std::max(iu->second.second, hi)};
                     }
                 }
             }
         }
     }
-    std::vector<int> ptr((size_t)P + 1, 0);
-    std::vector<int4> ent;
+    std::vector<int> ptr((size_t)P + 1, 0), uptr((size_t)P + 1, 0);
+    std::vector<int4> ent, uent;
     for (long long p = 0; p < P; ++p) {
         const auto& m = tm[(size_t)p];
         for (auto it = m.begin(); it != m.end(); ++it) {
@@ -707,20 +777,46 @@ static int build_templates(bf_abstraction* a, cudaStream_t st) {
             ent.push_back(make_int4(q, d1, (lo & 0xFFFF) | (hi << 16), cov));
         }
         ptr[(size_t)p + 1] = (int)ent.size();
+        const auto& mu_ = tu[(size_t)p];
+        for (auto it = mu_.begin(); it != mu_.end(); ++it) {
+            const int u = std::get<0>(it->first), q = std::get<1>(it->first), d1 = std::get<2>(it->first);
+            const int lo = it->second.first, hi = it->second.second;
+            auto nx = mu_.find(std::make_tuple(u, q, d1 + 1));
+            const int cov = (nx != mu_.end() && nx->second.first <= lo && nx->second.second >= hi) ? 1 : 0;
+            uent.push_back(make_int4(q, d1, (lo & 0xFFFF) | (hi << 16), cov | (u << 8)));
+        }
+        uptr[(size_t)p + 1] = (int)uent.size();
     }
-    int* dptr = nullptr;
-    int4* dent = nullptr;
-    BF_CUDA(cudaMalloc((void**)&dptr, sizeof(int) * ptr.size()));
-    cudaError_t e = cudaMalloc((void**)&dent, sizeof(int4) * std::max<size_t>(1, ent.size()));
+    int *dptr = nullptr, *duptr = nullptr;
+    int4 *dent = nullptr, *duent = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dptr, sizeof(int) * ptr.size());
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dent, sizeof(int4) * std::max<size_t>(1, ent.size()));
     if (e == cudaSuccess) e = cudaMemcpyAsync(dptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !ent.empty())
         e = cudaMemcpyAsync(dent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && g.U <= 32) {
+        e = cudaMalloc((void**)&duptr, sizeof(int) * uptr.size());
+        if (e == cudaSuccess) e = cudaMalloc((void**)&duent, sizeof(int4) * std::max<size_t>(1, uent.size()));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(duptr, uptr.data(), sizeof(int) * uptr.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !uent.empty())
+            e = cudaMemcpyAsync(duent, uent.data(), sizeof(int4) * uent.size(), cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { cudaFree(dptr); cudaFree(dent); return bfh::cuda_fail(e, "predecessor templates"); }
+    if (e != cudaSuccess) {
+        cudaFree(dptr); cudaFree(dent); cudaFree(duptr); cudaFree(duent);
+        return bfh::cuda_fail(e, "predecessor templates");
+    }
     a->d_tptr = dptr;
     a->d_tent = dent;
     a->tmpl_rows = P ? (double)ent.size() / (double)P : 0.0;
     a->bytes += sizeof(int) * ptr.size() + sizeof(int4) * ent.size();
+    if (duptr) {
+        a->d_uptr = duptr;
+        a->d_uent = duent;
+        a->utmpl_rows = P ? (double)uent.size() / (double)P : 0.0;
+        a->bytes += sizeof(int) * uptr.size() + sizeof(int4) * uent.size();
+    }
     return BF_OK;
 }
 
@@ -752,10 +848,12 @@ extern "C" void abs_free(bf_abstraction* a) {
     cudaFree(a->d_inputs);
     cudaFree(a->d_rk);
     cudaFree(a->d_shape);
-    cudaFree(a->d_poffs[0]);
-    cudaFree(a->d_poffs[1]);
+    for (int k = 0; k < 4; ++k) cudaFree(a->d_poffs[k]);
+    cudaFree(a->d_fmask);
     cudaFree(a->d_tptr);
     cudaFree(a->d_tent);
+    cudaFree(a->d_uptr);
+    cudaFree(a->d_uent);
     delete a;
 }
 

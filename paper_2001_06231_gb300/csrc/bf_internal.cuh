@@ -229,8 +229,13 @@ struct bf_abstraction {
     unsigned long long* d_shape;
     long long nplanes;
     long long shape_mismatch; // non-blocked records that differ from their plane's entry
-    int* d_poffs[2];          // lookup lists of every (plane, input) without / with the 3 x 3
-                              // window table [nplanes][U][kPlaneEnt] (solve_core.cuh), or NULL
+    int* d_poffs[4];          // lookup lists of every (plane, input) [nplanes][U][kPlaneEnt]
+                              // (solve_core.cuh), or NULL: [0] without the 3 x 3 window table,
+                              // [1] with it, [2] / [3] with it and the plane-pair table along
+                              // dim 2 / dim 3 (grids of 3+ / 4 dims)
+    // per cell the inputs whose record is the plane's entry (bits 0..31) and
+    // those with another record (bits 32..63); NULL where U > 32
+    unsigned long long* d_fmask;   // [C]
     // predecessor templates (shape table with no mismatch): per target plane p
     // the rows (source plane q, dim-1 offset d1, dim-0 offsets lo..hi) whose
     // cells x = (y0 + lo .. y0 + hi, y1 + d1, q) hold pred(y) for every cell
@@ -239,6 +244,12 @@ struct bf_abstraction {
     int* d_tptr;              // [nplanes + 1]
     int4* d_tent;             // [d_tptr[nplanes]]
     double tmpl_rows;         // mean template entries per plane
+    // per-input templates (U <= 32): the same rows kept apart by input, entries
+    // int4 {q, d1, lo & 0xFFFF | hi << 16, flags | u << 8} (flags bit 0: row
+    // (q, d1 + 1) of input u spans lo..hi too); NULL otherwise
+    int* d_uptr;              // [nplanes + 1]
+    int4* d_uent;             // [d_uptr[nplanes]]
+    double utmpl_rows;        // mean per-input template entries per plane
     // predecessor index [C][2*D] int16 offsets (x = y + off), empty: lo0 > hi0
     short* d_pred;
     double pred_rows;         // mean dim-0 rows of a predecessor box (cells with one)

@@ -43,6 +43,16 @@ struct bf_solve_ws {
     long long* M2 = nullptr;
     long long* M3 = nullptr;
     long long* M33 = nullptr;       // D >= 2: 3 x 3 windows on dims 0-1 (not with a successor class)
+    long long* M33P = nullptr;      // plane-pair table (allocated when a schedule first asks for it)
+    int pz = 0;                     // its dim (2 .. D - 1), 0: the gathers do not read it
+    int masked = 0;                 // the plane relax reads the cell masks: 1 = inputs in turn (two
+                                    // or four per iteration by `pair`), 2 = the pairs queued over the
+                                    // lanes (one or two per lane and round by `pair`)
+    int pm_blocks_full[2] = {0, 0}; // one full wave of the masked plane relax kernel, by `pair`
+    int pq_blocks_full[2] = {0, 0}; // the same for the pair-queue kernel
+    bool pfront = false;            // per-input frontier (with the per-input templates)
+    unsigned* ubits = nullptr;      // [U][S] (allocated when a schedule first asks for it)
+    unsigned* imask = nullptr;      // [C]
     bool use33 = false;             // gathers read M33 (bf_tune may switch it on)
     bool use_plane = true;          // relax reads the plane lookup lists (when the abstraction has them)
     bool use_tmpl = true;           // marking reads the predecessor templates (when the abstraction has them)
@@ -103,7 +113,7 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     if (!w) return;
     if (w->exec) cudaGraphExecDestroy(w->exec);
     if (w->graph) cudaGraphDestroy(w->graph);
-    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->M2); cudaFree(w->M3); cudaFree(w->M33); cudaFree(w->mu);
+    cudaFree(w->Vkey); cudaFree(w->Vnew); cudaFree(w->M2); cudaFree(w->M3); cudaFree(w->M33); cudaFree(w->M33P); cudaFree(w->mu);
     cudaFree(w->fbits); cudaFree(w->cells); cudaFree(w->chg); cudaFree(w->Gint); cudaFree(w->ctr);
     cudaFree(w->stage_G); cudaFree(w->stage_T); cudaFree(w->stage_tgt); cudaFree(w->stage_avoid);
     cudaFree(w->stage_V); cudaFree(w->trace); cudaFree(w->stamp);
@@ -111,6 +121,8 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->rmask); cudaFree(w->GRint); cudaFree(w->VN); cudaFree(w->VR); cudaFree(w->M2R);
     cudaFree(w->M3R); cudaFree(w->stage_GR);
     cudaFree(w->f1bits);
+    cudaFree(w->ubits);
+    cudaFree(w->imask);
     cudaFree(w->fc[0]); cudaFree(w->fc[1]); cudaFree(w->fc_tag);
     if (w->tile) tile_free(w->tile);
     delete w;
@@ -142,6 +154,12 @@ __global__ void k_init_tables(InstView v) {
     }
 }
 
+__global__ void k_init_table_pair(InstView v) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < v.g.C;
+         c += (long long)gridDim.x * blockDim.x)
+        table33p_entry(v, c);
+}
+
 __global__ void k_init_counters(Counters* ctr, long long cap) {
     memset(ctr, 0, sizeof(Counters));
     ctr->cap = cap;
@@ -162,6 +180,10 @@ int relax_wave_hybrid(int D);
 // Relax on abstractions with plane lookup lists (solve_plane.cu).
 int plane_relax_wave(int D, bool pair, bool occ);
 void launch_relax_plane(const InstView& v, bool count, bool mark, bool pair, bool occ, int blocks, cudaStream_t st);
+int masked_relax_wave(int D, bool quad);
+void launch_relax_masked(const InstView& v, bool mark, bool quad, int blocks, cudaStream_t st);
+int queue_relax_wave(int D, int U, bool two);
+void launch_relax_queue(const InstView& v, bool mark, bool two, int blocks, cudaStream_t st);
 
 // Propagate (warp per changed cell): set F2's bits from the changed list
 // (set-up: the finite cells; the passes mark F2 inside relax).
@@ -249,7 +271,7 @@ static int full_wave(K kernel, int threads) {
 size_t solve_ws_bytes(const bf_abstraction* a) {
     const size_t C = (size_t)a->g.C, U = (size_t)a->g.U, S = (C + 31) / 32;
     const size_t slice = 2ull * kSliceTargetMax * (size_t)sm_count() * 8 * 8 * 32;
-    return C * (5 * 8 + 1 + 4 + 4) + 4 * S + 2 * 8 * C * U + 8 * C + 8 * C + 2 * C + slice * 12 + slice / 8 + 4 * S +
+    return C * (6 * 8 + 1 + 4 + 4 + 4) + 4 * S * (U + 1) + 2 * 8 * C * U + 8 * C + 8 * C + 2 * C + slice * 12 + slice / 8 + 4 * S +
            sizeof(Counters);
 }
 
@@ -292,11 +314,25 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
     v.M2 = w->M2;
     v.M3 = w->M3;
     v.M33 = (w->cls || !w->use33) ? nullptr : w->M33;   // the class tables have no 3 x 3 windows
-    if (!w->cls && w->use_plane) v.poffs = a->d_poffs[v.M33 ? 1 : 0];
+    if (v.M33 && w->pz >= 2 && w->M33P && a->d_poffs[w->pz]) {
+        v.M33P = w->M33P;
+        v.pz = w->pz;
+    }
+    if (!w->cls && w->use_plane) {
+        v.poffs = a->d_poffs[v.M33P ? v.pz : (v.M33 ? 1 : 0)];
+        if (w->masked) v.fmask = a->d_fmask;
+    }
     if (w->use_tmpl && a->d_tent) {
         v.tptr = a->d_tptr;
         v.tent = a->d_tent;
+        if (w->pfront && a->d_uent && w->ubits && !w->cls) {
+            v.uptr = a->d_uptr;
+            v.uent = a->d_uent;
+            v.ubits = w->ubits;
+            v.imask = w->imask;
+        }
     }
+    v.nwords = w->nwords;
     if (w->fc_cap > 0) {
         v.fc[0] = w->fc[0];
         v.fc[1] = w->fc[1];
@@ -345,6 +381,16 @@ struct PassTimers {
 template <int D, int FMT>
 static void launch_relax(bf_solve_ws* w, const InstView& v, cudaStream_t st, bool count) {
     if constexpr (FMT == kBoxCompact && D >= 2) {
+        if (v.fmask && !count && v.poffs && v.g.U <= kPlaneUMax) {
+            const int full = (w->masked == 2 ? w->pq_blocks_full : w->pm_blocks_full)[w->pair ? 1 : 0];
+            if (full > 0) {
+                int b = (int)(((long long)w->relax_blocks * full + w->relax_blocks_full - 1) / w->relax_blocks_full);
+                if (b < 1) b = 1;
+                if (w->masked == 2) launch_relax_queue(v, w->fuse_mark, w->pair, b, st);
+                else launch_relax_masked(v, w->fuse_mark, w->pair, b, st);
+                return;
+            }
+        }
         const int form = count ? 0 : (w->pair ? 1 : 0) + (w->occ ? 2 : 0);
         const int full = w->pl_blocks_full[form];
         if (v.poffs && v.g.U <= kPlaneUMax && full > 0) {
@@ -408,6 +454,11 @@ template <int D>
 static void set_blocks(const bf_abstraction* a, bf_solve_ws* w) {
     if (D >= 2 && a->box_fmt == kBoxCompact && a->d_shape && a->g.U <= kPlaneUMax) {
         for (int f = 0; f < 4; ++f) w->pl_blocks_full[f] = plane_relax_wave(D, f & 1, f >> 1);
+        if (a->d_fmask)
+            for (int f = 0; f < 2; ++f) {
+                w->pm_blocks_full[f] = masked_relax_wave(D, f != 0);
+                w->pq_blocks_full[f] = queue_relax_wave(D, a->g.U, f != 0);
+            }
     }
     w->relax_blocks = a->box_fmt == kBoxRecompute ? relax_wave_recompute(D)
                       : a->box_fmt == kBoxHybrid ? relax_wave_hybrid(D) : relax_wave_stored(D, a->box_fmt);
@@ -433,6 +484,10 @@ static int ws_blocks(const bf_abstraction* a, bf_solve_ws* w, cudaStream_t st) {
     long long warps = w->relax_blocks;
     for (int i = 0; i < 4; ++i)
         if (w->pl_blocks_full[i] > warps) warps = w->pl_blocks_full[i];
+    for (int i = 0; i < 2; ++i) {
+        if (w->pm_blocks_full[i] > warps) warps = w->pm_blocks_full[i];
+        if (w->pq_blocks_full[i] > warps) warps = w->pq_blocks_full[i];
+    }
     warps *= 8;
     const long long cap = 2LL * kSliceTargetMax * warps * 32;
     cudaError_t e = cudaMalloc((void**)&w->cand_key, sizeof(long long) * cap);
@@ -601,6 +656,8 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     // set-up: lines 1-10 of Algorithm 1
     k_init_counters<<<1, 1, 0, st>>>(w->ctr, cap);
     BF_CUDA(cudaMemsetAsync(w->fbits, 0, 4 * w->nwords, st));
+    InstView v = make_view(a, w);
+    if (v.ubits) BF_CUDA(cudaMemsetAsync(w->ubits, 0, 4 * w->nwords * U, st));
     if (w->fc_cap > 0) BF_CUDA(cudaMemsetAsync(w->fc_tag, 0, 8 * C, st));    // no cell cached before pass 0
     k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dG, (const unsigned char*)dAv,
                                                      w->Gint, w->ctr);
@@ -614,9 +671,9 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     k_init_values<<<blocks_for(C, 256), 256, 0, st>>>(C, (const double*)dT, (const unsigned char*)dTgt,
                                                       (const unsigned char*)dAv, w->Vkey, w->Vnew, w->mu,
                                                       w->chg, count ? w->stamp : nullptr, w->ctr);
-    InstView v = make_view(a, w);
     if (count) v.stamp = w->stamp;
     k_init_tables<<<blocks_for(C, 256), 256, 0, st>>>(v);
+    if (v.M33P) k_init_table_pair<<<blocks_for(C, 256), 256, 0, st>>>(v);
     launch_setup_frontier(a, w, v, st);
     BF_CUDA(cudaGetLastError());
     double relax_ms = 0.0, prop_ms = 0.0;
@@ -678,9 +735,11 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
         // set-up: counters, costs, values, tables, first propagate, first
         // compaction, loop condition (graph); two or three kernels per pass;
         // output
-        o->kernel_launches = (host_loop ? 7 : 8) + ((w->fuse_mark ? 2 : 3) + (v.f1bits && !count ? 1 : 0)) * hc.round;
+        o->kernel_launches = (host_loop ? 7 : 8) + (v.M33P ? 1 : 0) +
+                             ((w->fuse_mark ? 2 : 3) + (v.f1bits && !count ? 1 : 0)) * hc.round;
         o->relaxed_cells = hc.total_relaxed;
-        o->executed_pairs = hc.total_relaxed * U;
+        // pairs taken up: counted by the masked relax, else every input of a relaxed cell
+        o->executed_pairs = (v.fmask && !count) ? hc.total_pairs : hc.total_relaxed * U;
         o->exact_f1_cells = count ? hc.total_exact : -1;
         o->changed_cells = hc.total_changed;
         o->relax_launches = hc.round;
@@ -747,12 +806,42 @@ struct Sched {
     bool pair = false;
     bool occ = false;
     int dense = 0;
+    int masked = 0;
+    int pz = 0;
+    bool pfront = false;
 };
+
+static bool same_sched(const Sched& x, const Sched& y) {
+    return x.slice == y.slice && x.fuse == y.fuse && x.blocks == y.blocks && x.use33 == y.use33 &&
+           x.plane == y.plane && x.tmpl == y.tmpl && x.pair == y.pair && x.occ == y.occ && x.dense == y.dense &&
+           x.masked == y.masked && x.pz == y.pz && x.pfront == y.pfront;
+}
 
 static bool base_plane_on(const Sched& s) { return s.plane; }
 
-static void set_schedule(bf_solve_ws* w, const Sched& s) {
+// Put schedule s in force; the plane-pair table is allocated on first use
+// (without memory the schedule goes without it).
+static void set_schedule(const bf_abstraction* a, bf_solve_ws* w, const Sched& s) {
     std::lock_guard<std::mutex> lock(w->mtx);
+    int pz = (s.pz >= 2 && s.pz < w->D && s.pz < 4 && a->d_poffs[s.pz]) ? s.pz : 0;
+    if (pz && !w->M33P && cudaMalloc((void**)&w->M33P, 8 * w->C) != cudaSuccess) {
+        cudaGetLastError();
+        w->M33P = nullptr;
+        pz = 0;
+    }
+    w->pz = pz;
+    w->masked = a->d_fmask != nullptr ? s.masked : 0;
+    bool pf = s.pfront && a->d_uent != nullptr;
+    if (pf && !w->ubits) {
+        if (cudaMalloc((void**)&w->ubits, 4 * w->nwords * w->U) != cudaSuccess ||
+            cudaMalloc((void**)&w->imask, 4 * w->C) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(w->ubits);
+            w->ubits = nullptr;
+            pf = false;
+        }
+    }
+    w->pfront = pf;
     w->slice_target = s.slice;
     w->fuse_mark = s.fuse;
     w->relax_blocks = s.blocks;
@@ -804,17 +893,48 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     b.pair = w->pair;
     b.occ = w->occ;
     b.dense = w->dense_pct;
+    b.masked = w->masked;
+    b.pz = w->pz;
+    b.pfront = w->pfront;
     out->default_ms = best;
     int tried = 1;
     const bool cls = opts && opts->succ_class;
     const bool has33 = w->M33 && !cls, hasp = a->d_poffs[0] && !cls, hast = a->d_tent != nullptr;
     const bool hasd = !cls && ws_tile(a, w, st) == BF_OK;
+    // two whole schedules first (the pair-queue relax, with the per-input
+    // frontier and marking in its own launch, or without it and marking in
+    // relax): their settings help each other, which one dimension at a time
+    // would not find
+    if (hasp && has33 && a->d_fmask) {
+        for (int k = 0; k < 2 && rc == BF_OK; ++k) {
+            Sched c = b;
+            c.use33 = true;
+            c.plane = true;
+            c.tmpl = hast;
+            c.masked = 2;
+            c.pair = true;
+            c.pfront = k == 0 && a->d_uent != nullptr;
+            c.fuse = k != 0;
+            if (same_sched(c, b)) continue;
+            set_schedule(a, w, c);
+            double ms = 0.0;
+            rc = tune_time(a, G, target, avoid, &o, V, mu, st, &ms);
+            ++tried;
+            if (rc == BF_OK && ms < best) {
+                best = ms;
+                b = c;
+            }
+        }
+    }
     // coordinate descent: each dimension's values with the others at the best
     // so far, two rounds
     for (int round = 0; round < 2 && rc == BF_OK; ++round) {
-        for (int dim = 0; dim < 9 && rc == BF_OK; ++dim) {
-            const int nval = (dim == 0 || dim == 7) ? (dim == 0 ? 4 : 3) : 2;
+        for (int dim = 0; dim < 12 && rc == BF_OK; ++dim) {
+            const int nval = (dim == 0 || dim == 9) ? 4 : (dim == 7 ? 3 : (dim == 10 ? a->g.D - 1 : 2));
             if (dim == 7 && !hasd) continue;
+            if (dim == 9 && !(hasp && a->d_fmask && base_plane_on(b))) continue;
+            if (dim == 10 && !(hasp && has33 && a->g.D >= 3 && base_plane_on(b) && b.use33)) continue;
+            if (dim == 11 && !(a->d_uent && b.tmpl)) continue;
             if (dim == 8 && !(hasp && base_plane_on(b))) continue;
             if ((dim == 3 && !has33) || (dim == 4 && !hasp) || (dim == 5 && !hast)) continue;
             if (dim == 6 && !(hasp && base_plane_on(b))) continue;
@@ -831,13 +951,16 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
                     case 5: c.tmpl = k != 0; break;
                     case 6: c.pair = k != 0; break;
                     case 7: c.dense = k == 0 ? 0 : (k == 1 ? 15 : 35); break;
-                    default: c.occ = k != 0; break;
+                    case 8: c.occ = k != 0; break;
+                    case 9:      // cell masks, with the per-input frontier for the queue form
+                        c.masked = k < 3 ? k : 2;
+                        if (k == 3) c.pfront = a->d_uent != nullptr && b.tmpl;
+                        break;
+                    case 10: c.pz = k == 0 ? 0 : k + 1; break;
+                    default: c.pfront = k != 0; break;
                 }
-                if (c.slice == base.slice && c.fuse == base.fuse && c.blocks == base.blocks &&
-                    c.use33 == base.use33 && c.plane == base.plane && c.tmpl == base.tmpl && c.pair == base.pair &&
-                    c.dense == base.dense && c.occ == base.occ)
-                    continue;
-                set_schedule(w, c);
+                if (same_sched(c, base)) continue;
+                set_schedule(a, w, c);
                 double ms = 0.0;
                 rc = tune_time(a, G, target, avoid, &o, V, mu, st, &ms);
                 ++tried;
@@ -848,7 +971,7 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
             }
         }
     }
-    set_schedule(w, b);
+    set_schedule(a, w, b);
     cudaFree(V);
     cudaFree(mu);
     if (rc) return rc;
@@ -861,6 +984,9 @@ extern "C" int bf_tune(const bf_abstraction* a, const double* G, const uint8_t* 
     out->pair_inputs = (b.pair && b.plane && hasp) ? 1 : 0;
     out->dense_pct = hasd ? b.dense : 0;
     out->occupancy = (b.occ && b.plane && hasp) ? 1 : 0;
+    out->cell_masks = (b.plane && hasp) ? w->masked : 0;
+    out->pair_dim = (w->pz && b.use33 && b.plane && hasp) ? w->pz : 0;
+    out->input_frontier = (w->pfront && b.tmpl && hast) ? 1 : 0;
     out->candidates = tried;
     out->best_ms = best;
     return BF_OK;
@@ -895,11 +1021,22 @@ extern "C" int bf_set_schedule(const bf_abstraction* a, const bf_tune_result* sc
     c.pair = sched->pair_inputs != 0;
     c.dense = sched->dense_pct;
     c.occ = sched->occupancy != 0;
+    c.masked = sched->cell_masks;
+    if (c.masked < 0 || c.masked > 2) {
+        bfh::set_error("bf_set_schedule: cell_masks %d outside 0..2", c.masked);
+        return BF_ERR_INVALID;
+    }
+    c.pz = sched->pair_dim;
+    c.pfront = sched->input_frontier != 0;
+    if (c.pz != 0 && (c.pz < 2 || c.pz >= a->g.D)) {
+        bfh::set_error("bf_set_schedule: pair_dim %d outside 0, 2 .. D - 1", c.pz);
+        return BF_ERR_INVALID;
+    }
     if (c.dense < 0 || c.dense > 100) {
         bfh::set_error("bf_set_schedule: dense_pct %d outside 0..100", c.dense);
         return BF_ERR_INVALID;
     }
     if (c.dense > 0 && ws_tile(a, w, (cudaStream_t)stream) != BF_OK) c.dense = 0;
-    set_schedule(w, c);
+    set_schedule(a, w, c);
     return BF_OK;
 }

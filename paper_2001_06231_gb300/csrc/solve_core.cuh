@@ -9,6 +9,10 @@
 //                          equal to V's windows at the start of every pass
 //   M33         int64 [C]  (single solve) max of V over y0..y0+2 x y1..y1+2 on
 //                          dims 0-1 (wrapping on periodic dims), same refresh
+//   M33P        int64 [C]  (single solve, optional) max(M33(y), M33(y + e_z)) for
+//                          one dim z >= 2 (the plane-pair dim; wrapping on a
+//                          periodic z, M33(y) alone on a non-periodic z's last
+//                          index), same refresh
 //   fbits       u32 [S]    upcoming frontier F2, one bit per cell
 //   cells       i32 [C]    current frontier F1 as a compacted cell list
 //   chg         i32 [C]    cells whose W decreased in the current pass
@@ -59,6 +63,8 @@ struct Counters {
     long long total_relaxed;  // summed over passes
     long long exact;          // cells of the exact F1 in the current pass (counting mode)
     long long total_exact;
+    long long pairs;          // (cell, input) pairs the masked relax took up in the current pass
+    long long total_pairs;
     long long total_changed;
     unsigned blocks_done;     // blocks of the running compact launch that finished
     int done;                 // loop condition became false
@@ -80,6 +86,9 @@ struct InstView {
     // offsets of its box's table lookups (plane_offsets), or NULL
     const unsigned long long* shape;   // [P][U]
     const int* poffs;                  // [P][U][kPlaneEnt]
+    // per cell: bit u (u < 32) = the pair (c, u) has a box and its record is
+    // the plane's entry; bit 32 + u = a box with another record; or NULL
+    const unsigned long long* fmask;   // [C]
     // predecessor templates per target plane (marking), or NULL: bounding boxes
     const int* tptr;                   // [P + 1]
     const int4* tent;
@@ -89,8 +98,19 @@ struct InstView {
     long long* M2;              // [C]
     long long* M3;              // [C]
     long long* M33;             // [C] max of V over 3 x 3 cells on dims 0-1, or NULL
+    long long* M33P;            // [C] max of M33 over two planes along dim pz, or NULL
+    int pz;                     // plane-pair dim (2 .. D - 1) of M33P, 0: none
     unsigned char* mu;          // [C]
     unsigned* fbits;            // [S]
+    // per-input frontier (per-input templates, U <= 32): the upcoming frontier
+    // as one bitmap per input (the pairs (x, u) whose box holds a changed
+    // cell), and per place of the frontier list the inputs to relax; NULL: the
+    // cell frontier fbits, every input of a frontier cell
+    const int* uptr;            // [P + 1] per-input templates
+    const int4* uent;
+    unsigned* ubits;            // [U][S]
+    unsigned* imask;            // [C]
+    long long nwords;           // S
     int* cells;                 // [C]
     int* chg;                   // [C]
     Counters* ctr;
@@ -127,8 +147,9 @@ struct InstView {
 };
 
 // Plane lookup list entry: int 0 = L | table << 8 (L = 0: no list, the
-// lanes take the general gather), ints 4 .. 4 + L4 - 1 the offsets of the L
-// lookups from the cell, L4 = L rounded up to 4 (padded with the first).
+// lanes take the general gather; table 0..4 = V, M2, M3, M33, M33P), ints
+// 4 .. 4 + L4 - 1 the offsets of the L lookups from the cell, L4 = L rounded
+// up to 4 (padded with the first).
 constexpr int kPlaneEnt = 4 + 28;
 constexpr int kPlaneMaxLook = 28;
 
@@ -159,6 +180,9 @@ inline void view_from_abs(InstView& v, const bf_abstraction* a) {
     v.pred = a->d_pred;
     v.shape = a->d_shape;
     v.poffs = nullptr;            // set by the solve that built the lists
+    v.fmask = nullptr;            // set by the solve when it relaxes by cell masks
+    v.M33P = nullptr;             // set by the solve that keeps the plane-pair table
+    v.pz = 0;
     v.tptr = nullptr;             // set by the solve when it marks with templates
     v.tent = nullptr;
 }
@@ -412,10 +436,15 @@ __device__ __forceinline__ int plane_of_cell(const GridDesc& g, long long x) {
 // Lookup list of record r on plane p (the lookups box_max_rows makes for a
 // lane of that plane, as offsets from the cell); the table is M33 when m33
 // and the box is at least 3 cells wide on dims 0 and 1, else V / M2 / M3 by
-// the width on dim 0.  Dims 0 and 1 are not periodic here; periodic dims >= 2
-// wrap with the plane's coordinates.
+// the width on dim 0.  With a plane-pair dim pz (2 .. D - 1; 0: none) a box
+// that reads M33 and spans at least 2 planes on dim pz reads M33P instead, at
+// ceil(w_pz / 2) positions along pz (the last one shifted back to end on the
+// box's last plane: the windows may overlap, the maximum is the same).  Dims
+// 0 and 1 are not periodic here; periodic dims >= 2 wrap with the plane's
+// coordinates.
 template <int D>
-__device__ __forceinline__ void plane_offsets(const GridDesc& g, unsigned long long r, int p, bool m33, int* out) {
+__device__ __forceinline__ void plane_offsets(const GridDesc& g, unsigned long long r, int p, bool m33, int pz,
+                                              int* out) {
     out[0] = 0;
     if ((rec_byte(r, 1) & 0x7F) == 0) return;                 // no pair of the plane
     int w[4] = {1, 1, 1, 1}, rel[4] = {0, 0, 0, 0}, k[4] = {0, 0, 0, 0};
@@ -426,10 +455,14 @@ __device__ __forceinline__ void plane_offsets(const GridDesc& g, unsigned long l
     }
     if (D >= 3) { k[2] = p % g.n[2]; k[3] = p / g.n[2]; }
     const bool use33 = m33 && D >= 2 && w[0] >= 3 && w[1] >= 3;
-    const int tab = use33 ? 3 : (w[0] == 1 ? 0 : (w[0] == 2 ? 1 : 2));
+    const bool usep = use33 && pz >= 2 && pz < D && w[pz] >= 2;
+    const int tab = usep ? 4 : (use33 ? 3 : (w[0] == 1 ? 0 : (w[0] == 2 ? 1 : 2)));
     const int np = w[0] < 3 ? 1 : (w[0] + 2) / 3;
     const int n1 = use33 ? (w[1] + 2) / 3 : w[1];
-    const long long L = (long long)np * n1 * w[2] * w[3];
+    // positions along dims 2 and 3 (steps of 2 along the pair dim)
+    int n23[4] = {1, 1, 1, 1};
+    for (int d = 2; d < D; ++d) n23[d] = (usep && d == pz) ? (w[d] + 1) / 2 : w[d];
+    const long long L = (long long)np * n1 * n23[2] * n23[3];
     if (L > kPlaneMaxLook) return;
     int lo[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -439,13 +472,14 @@ __device__ __forceinline__ void plane_offsets(const GridDesc& g, unsigned long l
         lo[d] = x;
     }
     int i = 0;
-    for (int j3 = 0; j3 < w[3]; ++j3)
-        for (int j2 = 0; j2 < w[2]; ++j2)
+    for (int j3 = 0; j3 < n23[3]; ++j3)
+        for (int j2 = 0; j2 < n23[2]; ++j2)
             for (int j1 = 0; j1 < n1; ++j1)
                 for (int q = 0; q < np; ++q) {
                     int off = rel[0] + (w[0] < 3 ? 0 : min(3 * q, w[0] - 3));
                     off += (rel[1] + (use33 ? min(3 * j1, w[1] - 3) : j1)) * (int)g.stride[1];
-                    const int j[4] = {0, 0, j2, j3};
+                    int j[4] = {0, 0, j2, j3};
+                    if (usep) j[pz] = min(2 * j[pz], w[pz] - 2);
 #pragma unroll
                     for (int d = 2; d < D; ++d) {
                         int x = lo[d] + j[d];
@@ -550,10 +584,14 @@ __device__ __forceinline__ void mark_box_rows(const InstView& v, const int* lo, 
 __device__ __forceinline__ void mark_template(const InstView& v, int p, int y0, int L, int y1, bool skip_cov) {
     const int lane = threadIdx.x & 31;
     const int n0 = v.g.n[0], n1 = v.g.n[1];
-    const int b = __ldg(v.tptr + p), e = __ldg(v.tptr + p + 1);
+    const bool per_input = v.ubits != nullptr;       // rows by input into that input's bitmap
+    const int* tp = per_input ? v.uptr : v.tptr;
+    const int4* te = per_input ? v.uent : v.tent;
+    const int b = __ldg(tp + p), e = __ldg(tp + p + 1);
     for (int i = b + lane; i < e; i += 32) {
-        const int4 t = __ldg(v.tent + i);
+        const int4 t = __ldg(te + i);
         if (skip_cov && (t.w & 1)) continue;
+        unsigned* bits = per_input ? v.ubits + (long long)(t.w >> 8) * v.nwords : v.fbits;
         const int r = y1 + t.y;
         if (r < 0 || r >= n1) continue;
         const int lo = (int)(short)(t.z & 0xFFFF), hi = t.z >> 16;
@@ -563,7 +601,7 @@ __device__ __forceinline__ void mark_template(const InstView& v, int p, int y0, 
         const int ca = base + a, cz = base + z;
         for (int wd = ca >> 5; wd <= (cz >> 5); ++wd) {
             const int lo_b = max(ca, wd << 5), hi_b = min(cz, (wd << 5) + 31);
-            mark_word(v.fbits, wd, bit_range(lo_b & 31, hi_b & 31));
+            mark_word(bits, wd, bit_range(lo_b & 31, hi_b & 31));
         }
     }
 }
@@ -602,7 +640,23 @@ __device__ __forceinline__ void propagate_entry(const InstView& v, int i, int nc
         }
         const unsigned rq = grid_div(g, 0, (unsigned)y0);
         const int y1 = (int)(rq - grid_div(g, 1, rq) * (unsigned)g.n[1]);
-        mark_template(v, plane_of_cell<D>(g, y0), k0, L, y1, false);
+        // the run's cells one dim-1 row down all changed in this pass (W not
+        // yet committed: Vnew != Vkey): the runs holding them mark every row
+        // a covered template entry would (dims 0 and 1 are not periodic here)
+        bool cov = false;
+        if (!commit && !v.inplace && y1 > 0) {
+            bool all = true;
+            for (int off = 0; off < L; off += 32) {
+                bool ok = true;
+                if (off + lane < L) {
+                    const long long yb = (long long)y0 + off + lane - n0;
+                    ok = v.Vnew[yb] != v.Vkey[yb];
+                }
+                all = __all_sync(0xFFFFFFFFu, ok) && all;
+            }
+            cov = all;
+        }
+        mark_template(v, plane_of_cell<D>(g, y0), k0, L, y1, cov);
         return;
     }
     // gather the run 32 places at a time; per lane min / max of the box ends
@@ -974,16 +1028,27 @@ constexpr int kPlaneUMax = 32;
 struct PlaneStage {
     int ent[kPlaneUMax][kPlaneEnt];
     unsigned long long rec[kPlaneUMax];
+    const long long* tab[kPlaneUMax];    // the table each list reads
 };
 
-// Copy the lists and records of plane p, inputs u0 .. u1 - 1, into st (whole warp).
+// The table of list header code t (bits 8.. of the header).
+__device__ __forceinline__ const long long* plane_table(const InstView& v, int t) {
+    return t == 4 ? v.M33P : (t == 3 ? v.M33 : (t == 2 ? v.M3 : (t == 1 ? v.M2 : v.Vkey)));
+}
+
+// Copy the lists, records and list tables of plane p, inputs u0 .. u1 - 1,
+// into st (whole warp).
 __device__ __forceinline__ void stage_plane(const InstView& v, int p, int u0, int u1, PlaneStage& st) {
     const int lane = threadIdx.x & 31;
     const int n = u1 - u0;
-    const int4* src = reinterpret_cast<const int4*>(v.poffs + ((long long)p * v.g.U + u0) * kPlaneEnt);
+    const int* lists = v.poffs + ((long long)p * v.g.U + u0) * kPlaneEnt;
+    const int4* src = reinterpret_cast<const int4*>(lists);
     int4* dst = reinterpret_cast<int4*>(&st.ent[0][0]);
     for (int i = lane; i < n * (kPlaneEnt / 4); i += 32) dst[i] = __ldg(src + i);
-    for (int i = lane; i < n; i += 32) st.rec[i] = __ldg(v.shape + (long long)p * v.g.U + u0 + i);
+    for (int i = lane; i < n; i += 32) {
+        st.rec[i] = __ldg(v.shape + (long long)p * v.g.U + u0 + i);
+        st.tab[i] = plane_table(v, __ldg(lists + (long long)i * kPlaneEnt) >> 8);
+    }
     __syncwarp();
 }
 
@@ -991,9 +1056,7 @@ __device__ __forceinline__ void stage_plane(const InstView& v, int p, int u0, in
 __device__ __forceinline__ long long plane_gather_s(const InstView& v, long long c, bool mine, const int* ent,
                                                     int hdr) {
     const int L4 = ((hdr & 0xFF) + 3) & ~3;
-    const int tab = hdr >> 8;
-    const long long* t = tab == 3 ? v.M33 : (tab == 2 ? v.M3 : (tab == 1 ? v.M2 : v.Vkey));
-    const long long* base = t + c;
+    const long long* base = plane_table(v, hdr >> 8) + c;
     const int4* o4 = reinterpret_cast<const int4*>(ent + 4);
     long long m0 = kKeyMin, m1 = kKeyMin, m2 = kKeyMin, m3 = kKeyMin;
     for (int i = 0; i < L4; i += 4) {
@@ -1015,9 +1078,8 @@ __device__ __forceinline__ long long plane_gather_s(const InstView& v, long long
 __device__ __forceinline__ void plane_gather2(const InstView& v, long long c, bool ma, const int* ea, int ha, bool mb,
                                               const int* eb, int hb, long long& ra, long long& rb) {
     const int La = ((ha & 0xFF) + 3) & ~3, Lb = ((hb & 0xFF) + 3) & ~3;
-    const int ta = ha >> 8, tb = hb >> 8;
-    const long long* pa = (ta == 3 ? v.M33 : (ta == 2 ? v.M3 : (ta == 1 ? v.M2 : v.Vkey))) + c;
-    const long long* pb = (tb == 3 ? v.M33 : (tb == 2 ? v.M3 : (tb == 1 ? v.M2 : v.Vkey))) + c;
+    const long long* pa = plane_table(v, ha >> 8) + c;
+    const long long* pb = plane_table(v, hb >> 8) + c;
     const int4* oa4 = reinterpret_cast<const int4*>(ea + 4);
     const int4* ob4 = reinterpret_cast<const int4*>(eb + 4);
     long long xa = kKeyMin, ya = kKeyMin, xb = kKeyMin, yb = kKeyMin;
@@ -1180,6 +1242,273 @@ __device__ __forceinline__ void relax_plane(const InstView& v, long long c, bool
     }
 }
 
+// relax_plane driven by the cell masks (fmask): per lane one 8-byte word says
+// which inputs have a box with the plane's record (the staged list applies)
+// and which have another record; only those pairs load their cost, and only
+// the second kind its record.  The inputs some lane of the plane group
+// relaxes go K at a time in increasing order with the lookups of all K in
+// flight (two per list per step) and the next K costs loaded meanwhile; the
+// comparison takes them in input order (lowest input among equal minima).
+template <int D, int K>
+__device__ __forceinline__ void relax_plane_m(const InstView& v, long long c, bool act, long long pos, int u0,
+                                              int u1, long long& best, int& bu, PlaneStage& st) {
+    const GridDesc& g = v.g;
+    const int pl = act ? plane_of_cell<D>(g, c) : -1;
+    const unsigned long long msk = act ? __ldcs(v.fmask + c) : 0ull;
+    unsigned range = (u1 >= 32 ? 0xFFFFFFFFu : ((1u << u1) - 1u)) & ~((1u << u0) - 1u);
+    // per-input frontier: only the pairs whose box holds a changed cell
+    if (v.imask && act) range &= __ldcs(v.imask + pos);
+    {
+        const unsigned taken = act ? (unsigned)__popc(range) : 0u;
+        const unsigned tw = __reduce_add_sync(0xFFFFFFFFu, taken);
+        if ((threadIdx.x & 31) == 0 && tw) atomicAdd((unsigned long long*)&v.ctr->pairs, (unsigned long long)tw);
+    }
+    const double* gp = v.Gint + c;
+    unsigned pend = __ballot_sync(0xFFFFFFFFu, act);
+    while (pend) {
+        const int p = __shfl_sync(0xFFFFFFFFu, pl, __ffs(pend) - 1);
+        const bool grp = act && pl == p;
+        pend &= ~__ballot_sync(0xFFFFFFFFu, grp);
+        const unsigned fast = grp ? (unsigned)msk & range : 0u;
+        const unsigned slow = grp ? (unsigned)(msk >> 32) & range : 0u;
+        const unsigned mine = fast | slow;
+        unsigned todo = __reduce_or_sync(0xFFFFFFFFu, mine);
+        if (!todo) continue;
+        stage_plane(v, p, u0, u1, st);
+        int un[K];
+        double gn[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            un[j] = todo ? __ffs(todo) - 1 : -1;
+            todo &= todo - 1u;
+            gn[j] = (un[j] >= 0 && ((mine >> un[j]) & 1u)) ? __ldcs(gp + (long long)un[j] * g.C) : 0.0;
+        }
+        while (un[0] >= 0) {
+            int uc[K];
+            double gc[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                uc[j] = un[j];
+                gc[j] = gn[j];
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                un[j] = todo ? __ffs(todo) - 1 : -1;
+                todo &= todo - 1u;
+                gn[j] = (un[j] >= 0 && ((mine >> un[j]) & 1u)) ? __ldcs(gp + (long long)un[j] * g.C) : 0.0;
+            }
+            // lookups of the K staged lists (warp-uniform lengths)
+            long long m[K];
+            int L[K];
+            bool f[K];
+            const int* off[K];
+            const long long* tb[K];
+            int Lmax = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                m[j] = kKeyMin;
+                const int e = uc[j] >= 0 ? uc[j] - u0 : 0;
+                L[j] = uc[j] >= 0 ? (st.ent[e][0] & 0xFF) : 0;
+                f[j] = uc[j] >= 0 && ((fast >> uc[j]) & 1u) && L[j] != 0;
+                off[j] = &st.ent[e][4];
+                tb[j] = st.tab[e] + c;
+                Lmax = L[j] > Lmax ? L[j] : Lmax;
+            }
+            for (int i = 0; i < Lmax; i += 2) {
+                long long a[K], b[K];
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    a[j] = kKeyMin;
+                    b[j] = kKeyMin;
+                    if (i < L[j]) {
+                        // entries past L up to L rounded to 4 repeat the first
+                        const int2 o = *reinterpret_cast<const int2*>(off[j] + i);
+                        if (f[j]) {
+                            a[j] = __ldg(tb[j] + o.x);
+                            b[j] = __ldg(tb[j] + o.y);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < K; ++j) m[j] = max(m[j], max(a[j], b[j]));
+            }
+            // the rare lanes: another record (box walk) or a list too long
+            // for the stage (one warp gather of the plane's record)
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if (uc[j] < 0) continue;
+                const bool sj = (slow >> uc[j]) & 1u;
+                const bool lj = ((fast >> uc[j]) & 1u) && L[j] == 0;
+                if (!__any_sync(0xFFFFFFFFu, sj || lj)) continue;
+                const unsigned lm = __ballot_sync(0xFFFFFFFFu, lj);
+                if (lm) {
+                    const long long lc = __shfl_sync(0xFFFFFFFFu, (int)c, __ffs(lm) - 1);
+                    const long long x = box_max_rows<D>(v, c, lj, st.rec[uc[j] - u0], lc);
+                    if (lj) m[j] = x;
+                }
+                if (sj) {
+                    const unsigned long long r =
+                        (unsigned long long)__ldcs(reinterpret_cast<const compact_t<D>*>(v.boxes) + c +
+                                                   (long long)uc[j] * g.C);
+                    m[j] = box_max<D>(v.Vkey, g, decode_compact<D>(r, g, c));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if (uc[j] < 0 || !((mine >> uc[j]) & 1u) || m[j] == kKeyInf) continue;   // +inf + G = +inf
+                const long long dk = key_of(gc[j] + val_of(m[j]));                       // the one FP64 add
+                if (dk < best) { best = dk; bu = uc[j]; }
+            }
+        }
+        __syncwarp();                                        // before the stage is overwritten
+    }
+}
+
+// Stage of the pair-queue relax (relax_plane_q), per warp: the lists,
+// records and list tables of the plane (inputs u0 .. u1 - 1 at rows u - u0),
+// the queue of (lane, input) pairs and the candidate of every pair.
+template <int UM>
+struct PairStage {
+    int ent[UM][kPlaneEnt];
+    unsigned long long rec[UM];
+    const long long* tab[UM];
+    long long cand[UM][32];            // [input - u0][lane]
+    unsigned short pairs[UM * 32];     // lane | input << 8, input-major
+    int plane, su0, su1;               // what ent / rec / tab hold (plane -1: nothing)
+    unsigned longm;                    // inputs whose list did not fit (header 0)
+};
+
+// relax_plane_m with the pairs spread over the lanes: the (lane, input) pairs
+// the staged lists serve (the lane's record is the plane's entry and the
+// per-input frontier, if any, holds the pair) go into a queue, input by
+// input; each round the 32 lanes take R pairs each -- consecutive cells of
+// one input, so the cost loads and the lookups stay coalesced -- and store
+// their candidates; pairs with another record, or a list too long for the
+// stage, walk their boxes on their own lanes.  Each lane then takes its
+// candidates in input order (strict decrease: the lowest input among equal
+// minima), so only the pairs a lane holds cost work, however sparse.
+template <int D, int UM, int R>
+__device__ __forceinline__ void relax_plane_q(const InstView& v, long long c, bool act, long long pos, int u0,
+                                              int u1, long long& best, int& bu, PairStage<UM>& st,
+                                              long long& taken) {
+    const int lane = threadIdx.x & 31;
+    const GridDesc& g = v.g;
+    const int pl = act ? plane_of_cell<D>(g, c) : -1;
+    const unsigned long long msk = act ? __ldcs(v.fmask + c) : 0ull;
+    unsigned range = (u1 >= 32 ? 0xFFFFFFFFu : ((1u << u1) - 1u)) & ~((1u << u0) - 1u);
+    if (v.imask && act) range &= __ldcs(v.imask + pos);
+    taken += act ? __popc(range) : 0;
+    const int ci = (int)c;
+    const long long C = g.C;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned pend = __ballot_sync(0xFFFFFFFFu, act);
+    while (pend) {
+        const int p = __shfl_sync(0xFFFFFFFFu, pl, __ffs(pend) - 1);
+        const bool grp = act && pl == p;
+        pend &= ~__ballot_sync(0xFFFFFFFFu, grp);
+        const unsigned fast = grp ? (unsigned)msk & range : 0u;
+        const unsigned slow = grp ? (unsigned)(msk >> 32) & range : 0u;
+        if (!__any_sync(0xFFFFFFFFu, (fast | slow) != 0u)) continue;
+        // stage the plane's lists (rows u - u0), unless the stage holds them
+        const int n = u1 - u0;
+        if (st.plane != p || st.su0 != u0 || st.su1 != u1) {
+            __syncwarp();
+            if (lane == 0) { st.plane = p; st.su0 = u0; st.su1 = u1; }
+            const int* lists = v.poffs + ((long long)p * g.U + u0) * kPlaneEnt;
+            const int4* src = reinterpret_cast<const int4*>(lists);
+            int4* dst = reinterpret_cast<int4*>(&st.ent[0][0]);
+            for (int i = lane; i < n * (kPlaneEnt / 4); i += 32) dst[i] = __ldg(src + i);
+            int hdr = 1;
+            for (int i = lane; i < n; i += 32) {
+                st.rec[i] = __ldg(v.shape + (long long)p * g.U + u0 + i);
+                hdr = __ldg(lists + (long long)i * kPlaneEnt);
+                st.tab[i] = plane_table(v, hdr >> 8);
+            }
+            // inputs whose list did not fit (header 0 on a plane entry with a box)
+            const unsigned lm = __ballot_sync(0xFFFFFFFFu, lane < n && (hdr & 0xFF) == 0) << u0;
+            if (lane == 0) st.longm = lm;
+        }
+        __syncwarp();
+        const unsigned longm = st.longm;
+        const unsigned fl = fast & ~longm;
+        const unsigned walk = slow | (fast & longm);
+        // queue the list pairs input by input
+        int np = 0;
+        unsigned todo = __reduce_or_sync(0xFFFFFFFFu, fl);
+        while (todo) {
+            const int u = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const bool has = (fl >> u) & 1u;
+            const unsigned b = __ballot_sync(0xFFFFFFFFu, has);
+            if (has) st.pairs[np + __popc(b & lt)] = (unsigned short)(lane | (u << 8));
+            np += __popc(b);
+        }
+        __syncwarp();
+        for (int k0 = 0; k0 < np; k0 += 32 * R) {
+            int s[R], e[R], L[R];
+            bool h[R];
+            double gv[R];
+            const long long* tb[R];
+            long long m[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int k = k0 + r * 32 + lane;
+                h[r] = k < np;
+                const unsigned q = h[r] ? st.pairs[k] : 0u;
+                s[r] = (int)(q & 31u);
+                const int u = (int)(q >> 8);
+                const int cs = __shfl_sync(0xFFFFFFFFu, ci, s[r]);
+                e[r] = h[r] ? u - u0 : 0;
+                L[r] = h[r] ? (st.ent[e[r]][0] & 0xFF) : 0;
+                tb[r] = st.tab[e[r]] + cs;
+                gv[r] = h[r] ? __ldcs(v.Gint + (long long)u * C + cs) : 0.0;
+                m[r] = kKeyMin;
+            }
+            int Lm = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) Lm = L[r] > Lm ? L[r] : Lm;
+            for (int i = 0; i < Lm; i += 2) {
+                long long a[R], b[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    a[r] = kKeyMin;
+                    b[r] = kKeyMin;
+                    if (i < L[r]) {
+                        // entries past L up to L rounded to 4 repeat the first
+                        const int2 o = *reinterpret_cast<const int2*>(&st.ent[e[r]][4 + i]);
+                        a[r] = __ldg(tb[r] + o.x);
+                        b[r] = __ldg(tb[r] + o.y);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) m[r] = max(m[r], max(a[r], b[r]));
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (h[r])    // +inf + G = +inf: no candidate
+                    st.cand[e[r]][s[r]] = m[r] == kKeyInf ? kKeyInf : key_of(gv[r] + val_of(m[r]));   // the one FP64 add
+        }
+        // the rare pairs: another record, or a list too long for the stage
+        for (unsigned wk = walk; wk; wk &= wk - 1u) {
+            const int u = __ffs(wk) - 1;
+            const unsigned long long r =
+                ((fast >> u) & 1u) ? st.rec[u - u0]
+                                   : (unsigned long long)__ldcs(reinterpret_cast<const compact_t<D>*>(v.boxes) + c +
+                                                                (long long)u * C);
+            const long long mm = box_max<D>(v.Vkey, g, decode_compact<D>(r, g, c));
+            const double gw = __ldcs(v.Gint + (long long)u * C + c);
+            st.cand[u - u0][lane] = mm == kKeyInf ? kKeyInf : key_of(gw + val_of(mm));
+        }
+        __syncwarp();
+        for (unsigned mine = fl | walk; mine; mine &= mine - 1u) {
+            const int u = __ffs(mine) - 1;
+            const long long dk = st.cand[u - u0][lane];
+            if (dk < best) { best = dk; bu = u; }
+        }
+        __syncwarp();                                        // before the stage is overwritten
+    }
+}
+
 // Write the result of a relaxed cell: Vnew, mu and the changed list; with
 // MARK also the predecessor boxes of the changed cells into the next frontier.
 template <int D, bool COUNT, bool MARK>
@@ -1215,16 +1544,22 @@ __device__ __forceinline__ FcLane fc_lane(const InstView& v, long long c, bool a
 // Returns the number of cells relaxed; in counting mode adds the cells of the
 // exact F1 (some box holds a cell changed in the previous pass) to *exact.
 // MARK: also set the next frontier's bits (no separate propagate launch).
-template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false, int PLANE = 0>
+template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false, int PLANE = 0, int UM = 16>
 __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int count, long long round, int* exact,
-                                           PlaneStage* st = nullptr) {
+                                           void* stv = nullptr, long long* taken = nullptr) {
+    PlaneStage* st = reinterpret_cast<PlaneStage*>(stv);
     const int lane = threadIdx.x & 31;
     const bool act = lane < count;
     const long long c = act ? v.cells[first + lane] : 0;
     long long best = act ? v.Vkey[c] : 0;
     int bu = -1;
     bool in_exact = false;
-    if constexpr (PLANE != 0) {
+    if constexpr (PLANE >= 5) {
+        relax_plane_q<D, UM, PLANE == 6 ? 2 : 1>(v, c, act, first + lane, 0, v.g.U, best, bu,
+                                                 *reinterpret_cast<PairStage<UM>*>(stv), *taken);
+    } else if constexpr (PLANE >= 3) {
+        relax_plane_m<D, PLANE == 4 ? 4 : 2>(v, c, act, first + lane, 0, v.g.U, best, bu, *st);
+    } else if constexpr (PLANE != 0) {
         relax_plane<D, COUNT, PLANE == 2>(v, c, act, 0, v.g.U, round, best, bu, in_exact, *st);
     } else if ((FMT == kBoxRecompute || FMT == kBoxHybrid) && v.fc_cap > 0) {
         FcLane fl = fc_lane(v, c, act, first + lane, round);
@@ -1243,9 +1578,10 @@ __device__ __forceinline__ int relax_chunk(const InstView& v, int first, int cou
 // smaller candidate -- the same lowest input among the smallest values as one
 // warp going through all inputs -- commits the cells and resets the counter.
 // Returns the cells relaxed (counted by the completing warp).
-template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false, int PLANE = 0>
+template <int D, int FMT, bool COUNT, bool MARK = false, bool CLS = false, int PLANE = 0, int UM = 16>
 __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, int sl, int S, int q, long long round,
-                                           int* exact, PlaneStage* st = nullptr) {
+                                           int* exact, void* stv = nullptr, long long* taken = nullptr) {
+    PlaneStage* st = reinterpret_cast<PlaneStage*>(stv);
     const int lane = threadIdx.x & 31;
     const int first = ch << 5;
     const int count = ncur - first;
@@ -1258,7 +1594,12 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
     const int u1 = min(v.g.U, u0 + q);
     FcLane fl;
     const bool fc = (FMT == kBoxRecompute || FMT == kBoxHybrid) && v.fc_cap > 0;
-    if constexpr (PLANE != 0) {
+    if constexpr (PLANE >= 5) {
+        relax_plane_q<D, UM, PLANE == 6 ? 2 : 1>(v, c, act, first + lane, u0, u1, best, bu,
+                                                 *reinterpret_cast<PairStage<UM>*>(stv), *taken);
+    } else if constexpr (PLANE >= 3) {
+        relax_plane_m<D, PLANE == 4 ? 4 : 2>(v, c, act, first + lane, u0, u1, best, bu, *st);
+    } else if constexpr (PLANE != 0) {
         relax_plane<D, COUNT, PLANE == 2>(v, c, act, u0, u1, round, best, bu, in_exact, *st);
     } else if (fc) {
         fl = fc_lane(v, c, act, first + lane, round);
@@ -1295,7 +1636,7 @@ __device__ __forceinline__ int relax_slice(const InstView& v, int ncur, int ch, 
 
 // One relax launch of the single solve (whole grid): warps take the chunks
 // of 32 frontier cells, or (small frontiers) (chunk, input slice) items.
-template <int D, int FMT, bool COUNT, bool MARK, bool CLS, int PLANE = 0>
+template <int D, int FMT, bool COUNT, bool MARK, bool CLS, int PLANE = 0, int UM = 16>
 __device__ __forceinline__ void relax_pass(const InstView& v) {
     Counters* k = v.ctr;
     if (k->done) return;
@@ -1317,20 +1658,33 @@ __device__ __forceinline__ void relax_pass(const InstView& v) {
         if ((long long)nchunks * S * 32 > v.slice_cap) { S = 1; q = U; }
     }
     const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
-    PlaneStage* st = nullptr;
-    if constexpr (PLANE != 0) {
+    void* st = nullptr;
+    if constexpr (PLANE >= 5) {
+        extern __shared__ __align__(16) unsigned char plane_smem[];
+        PairStage<UM>* ps = reinterpret_cast<PairStage<UM>*>(plane_smem) + (threadIdx.x >> 5);
+        if ((threadIdx.x & 31) == 0) ps->plane = -1;                // nothing staged yet
+        __syncwarp();
+        st = ps;
+    } else if constexpr (PLANE != 0) {
         extern __shared__ __align__(16) unsigned char plane_smem[];
         st = reinterpret_cast<PlaneStage*>(plane_smem) + (threadIdx.x >> 5);
     }
+    long long taken = 0;
     if (S == 1) {
         for (int ch = gw; ch < nchunks; ch += nwarps)
-            relaxed += relax_chunk<D, FMT, COUNT, MARK, CLS, PLANE>(v, ch << 5, ncur - (ch << 5), round, &exact, st);
+            relaxed += relax_chunk<D, FMT, COUNT, MARK, CLS, PLANE, UM>(v, ch << 5, ncur - (ch << 5), round,
+                                                                        &exact, st, &taken);
     } else {
         const int items = nchunks * S;
         for (int it = gw; it < items; it += nwarps) {
             const int ch = it / S;
-            relaxed += relax_slice<D, FMT, COUNT, MARK, CLS, PLANE>(v, ncur, ch, it - ch * S, S, q, round, &exact, st);
+            relaxed += relax_slice<D, FMT, COUNT, MARK, CLS, PLANE, UM>(v, ncur, ch, it - ch * S, S, q, round,
+                                                                        &exact, st, &taken);
         }
+    }
+    if constexpr (PLANE >= 5) {
+        const unsigned long long tw = __reduce_add_sync(0xFFFFFFFFu, (unsigned)taken);
+        if ((threadIdx.x & 31) == 0 && tw) atomicAdd((unsigned long long*)&k->pairs, tw);
     }
     if ((threadIdx.x & 31) == 0) {
         if (relaxed) atomicAdd((unsigned long long*)&k->relaxed, (unsigned long long)relaxed);
@@ -1422,6 +1776,80 @@ __device__ __forceinline__ void table33_entry(const InstView& v, long long e) {
     table33_at(v, e - x0 - (long long)x1 * n0, x0, x1);
 }
 
+// The nine 3 x 3 window maxima of Vnew holding cell (x, x1) of the dims-0/1
+// plane whose cell (0, 0) is base: out[b][a] = the window starting at
+// (x - a, x1 - b).  Vnew is read once over the 5 x 5 block around the cell
+// (cells outside a non-periodic edge count as kKeyMin, periodic dims wrap):
+// 3-cell row windows first, then 3-row column windows.
+__device__ __forceinline__ void windows33(const InstView& v, long long base, int x, int x1, long long out[3][3]) {
+    const GridDesc& g = v.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    long long w3[5][3];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        int r = x1 - 2 + i;
+        bool rin = true;
+        if (r < 0) { if (g.periodic[1]) r += n1; else rin = false; }
+        else if (r >= n1) { if (g.periodic[1]) r -= n1; else rin = false; }
+        if (rin && (r < 0 || r >= n1)) r = ((r % n1) + n1) % n1;   // n1 < 3 on a periodic dim
+        long long cv[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            int c = x - 2 + k;
+            bool cin = rin;
+            if (c < 0) { if (g.periodic[0]) c += n0; else cin = false; }
+            else if (c >= n0) { if (g.periodic[0]) c -= n0; else cin = false; }
+            if (cin && (c < 0 || c >= n0)) c = ((c % n0) + n0) % n0;
+            cv[k] = cin ? v.Vnew[base + (long long)r * n0 + c] : kKeyMin;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) w3[i][a] = max(cv[2 - a], max(cv[3 - a], cv[4 - a]));
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out[b][a] = max(w3[2 - b][a], max(w3[3 - b][a], w3[4 - b][a]));
+}
+
+// Write max(p[b][a], q[b][a]) to the window entries starting at (x - a,
+// x1 - b) of the plane at base (those inside a non-periodic edge).
+__device__ __forceinline__ void write33(const InstView& v, long long* t, long long base, int x, int x1,
+                                        const long long p[3][3], const long long q[3][3]) {
+    const GridDesc& g = v.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        int r = x1 - b;
+        if (r < 0) {
+            if (!g.periodic[1]) break;
+            r += n1;
+            if (r < 0) break;                     // n1 < 3: the entry repeats
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int c = x - a;
+            if (c < 0) {
+                if (!g.periodic[0]) break;
+                c += n0;
+                if (c < 0) break;
+            }
+            t[base + (long long)r * n0 + c] = max(p[b][a], q[b][a]);
+        }
+    }
+}
+
+// M33P at cell e from M33 (set-up, after every M33 entry is in place).
+__device__ __forceinline__ void table33p_entry(const InstView& v, long long e) {
+    const GridDesc& g = v.g;
+    const int z = v.pz;
+    const long long sz = g.stride[z];
+    const int kz = (int)((e / sz) % g.n[z]);
+    long long m = v.M33[e];
+    if (kz + 1 < g.n[z]) m = max(m, v.M33[e + sz]);
+    else if (g.periodic[z]) m = max(m, v.M33[e - (long long)kz * sz]);
+    v.M33P[e] = m;
+}
+
 __device__ __forceinline__ void refresh_tables(const InstView& v, long long y) {
     const GridDesc& g = v.g;
     const int n0 = g.n[0];
@@ -1437,51 +1865,28 @@ __device__ __forceinline__ void refresh_tables(const InstView& v, long long y) {
         table_entry(v, row + xe);
     }
     if (v.M33) {
-        // the 3 x 3 windows holding y start at (x - a, x1 - b), a, b in 0..2:
-        // read Vnew once over the 5 x 5 block around y (cells outside a
-        // non-periodic edge count as kKeyMin, periodic dims wrap), take the
-        // 3-cell row windows, then the 3-row column windows
         const int n1 = g.n[1];
         const int x1 = (int)(rq - (long long)grid_div(g, 1, (unsigned)rq) * n1);
         const long long base = row - (long long)x1 * n0;
-        long long w3[5][3];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            int r = x1 - 2 + i;
-            bool rin = true;
-            if (r < 0) { if (g.periodic[1]) r += n1; else rin = false; }
-            else if (r >= n1) { if (g.periodic[1]) r -= n1; else rin = false; }
-            if (rin && (r < 0 || r >= n1)) r = ((r % n1) + n1) % n1;   // n1 < 3 on a periodic dim
-            long long cv[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                int c = x - 2 + k;
-                bool cin = rin;
-                if (c < 0) { if (g.periodic[0]) c += n0; else cin = false; }
-                else if (c >= n0) { if (g.periodic[0]) c -= n0; else cin = false; }
-                if (cin && (c < 0 || c >= n0)) c = ((c % n0) + n0) % n0;
-                cv[k] = cin ? v.Vnew[base + (long long)r * n0 + c] : kKeyMin;
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) w3[i][a] = max(cv[2 - a], max(cv[3 - a], cv[4 - a]));
-        }
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            int r = x1 - b;
-            if (r < 0) {
-                if (!g.periodic[1]) break;
-                r += n1;
-                if (r < 0) break;                     // n1 < 3: the entry repeats
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                int c = x - a;
-                if (c < 0) {
-                    if (!g.periodic[0]) break;
-                    c += n0;
-                    if (c < 0) break;
-                }
-                v.M33[base + (long long)r * n0 + c] = max(w3[2 - b][a], max(w3[3 - b][a], w3[4 - b][a]));
+        long long mid[3][3];
+        windows33(v, base, x, x1, mid);
+        write33(v, v.M33, base, x, x1, mid, mid);
+        if (v.M33P) {
+            // the pair entries holding y's plane: (plane z, z + 1) and (z - 1, z)
+            const int z = v.pz;
+            const long long sz = g.stride[z];
+            const int nz = g.n[z];
+            const int kz = (int)((y / sz) % nz);
+            long long nb[3][3];
+            int zp = kz + 1;
+            if (zp >= nz) zp = g.periodic[z] ? zp - nz : -1;
+            if (zp >= 0) windows33(v, base + (long long)(zp - kz) * sz, x, x1, nb);
+            write33(v, v.M33P, base, x, x1, mid, zp >= 0 ? nb : mid);
+            int zm = kz - 1;
+            if (zm < 0) zm = g.periodic[z] ? zm + nz : -1;
+            if (zm >= 0 && zm != kz) {
+                windows33(v, base + (long long)(zm - kz) * sz, x, x1, nb);
+                write33(v, v.M33P, base + (long long)(zm - kz) * sz, x, x1, nb, mid);
             }
         }
     }
@@ -1501,9 +1906,27 @@ __device__ __forceinline__ void compact_words(const InstView& v, int w_begin, in
     const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
     const int wd = w_begin + t;
     unsigned bits = 0;
+    // per-input frontier: the word of every input (a cell is in the frontier
+    // when some input's bit is set), kept to give each cell its input mask
+    unsigned wv[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) wv[u] = 0u;
     if (wd < w_end) {
-        bits = v.fbits[wd];
-        if (bits) v.fbits[wd] = 0u;
+        if (v.ubits) {
+            const int U = v.g.U;
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                if (u < U) {
+                    unsigned* pw = v.ubits + (long long)u * v.nwords + wd;
+                    wv[u] = *pw;
+                    if (wv[u]) *pw = 0u;
+                    bits |= wv[u];
+                }
+            }
+        } else {
+            bits = v.fbits[wd];
+            if (bits) v.fbits[wd] = 0u;
+        }
         if (v.f1bits) v.f1bits[wd] = bits;
     }
     const int cnt = __popc(bits);
@@ -1532,6 +1955,17 @@ __device__ __forceinline__ void compact_words(const InstView& v, int w_begin, in
     while (bits) {
         const int b = __ffs(bits) - 1;
         bits &= bits - 1;
+        if (v.imask) {
+            unsigned m = 0u;
+            if (v.g.U <= 16) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) m |= ((wv[u] >> b) & 1u) << u;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 32; ++u) m |= ((wv[u] >> b) & 1u) << u;
+            }
+            v.imask[pos] = m;
+        }
         v.cells[pos++] = (int)(cbase + b);
     }
     __syncthreads();                                      // before warp_sum / block_base are reused
@@ -1555,6 +1989,8 @@ __device__ __forceinline__ int finish_pass(const InstView& v) {
     }
     k->total_relaxed += k->relaxed;
     k->total_exact += k->exact;
+    k->total_pairs += k->pairs;
+    k->pairs = 0;
     k->total_changed += k->nchg;
     k->relaxed = 0;
     k->exact = 0;
