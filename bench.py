@@ -310,8 +310,10 @@ def ours(args, rank, world, local_rank):
     rt = solve(time_kernels=True)
     relax_ms_avg = rt["stats"]["relax_ms"] / max(1, rt["stats"]["relax_launches"])
     prop_ms_avg = rt["stats"]["propagate_ms"] / max(1, rt["stats"]["relax_launches"])
-    if sched != bf.SCHED_JACOBI:               # executed work and passes of the timed schedule
-        executed = rt["stats"]["executed_pairs"]
+    # executed work of the timed relax form (the counting solve relaxes every
+    # input of each frontier cell); passes of the timed schedule
+    executed = rt["stats"]["executed_pairs"]
+    if sched != bf.SCHED_JACOBI:
         passes = rt["iters"]
 
     for _ in range(args.warmup):

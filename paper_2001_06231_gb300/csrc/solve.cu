@@ -51,8 +51,7 @@ struct bf_solve_ws {
     int pm_blocks_full[2] = {0, 0}; // one full wave of the masked plane relax kernel, by `pair`
     int pq_blocks_full[2] = {0, 0}; // the same for the pair-queue kernel
     bool pfront = false;            // per-input frontier (with the per-input templates)
-    unsigned* ubits = nullptr;      // [U][S] (allocated when a schedule first asks for it)
-    unsigned* imask = nullptr;      // [C]
+    unsigned* ubits = nullptr;      // [2][U][S] (allocated when a schedule first asks for it)
     bool use33 = false;             // gathers read M33 (bf_tune may switch it on)
     bool use_plane = true;          // relax reads the plane lookup lists (when the abstraction has them)
     bool use_tmpl = true;           // marking reads the predecessor templates (when the abstraction has them)
@@ -122,7 +121,6 @@ void bf_solve_ws_free(bf_solve_ws* w) {
     cudaFree(w->M3R); cudaFree(w->stage_GR);
     cudaFree(w->f1bits);
     cudaFree(w->ubits);
-    cudaFree(w->imask);
     cudaFree(w->fc[0]); cudaFree(w->fc[1]); cudaFree(w->fc_tag);
     if (w->tile) tile_free(w->tile);
     delete w;
@@ -271,7 +269,7 @@ static int full_wave(K kernel, int threads) {
 size_t solve_ws_bytes(const bf_abstraction* a) {
     const size_t C = (size_t)a->g.C, U = (size_t)a->g.U, S = (C + 31) / 32;
     const size_t slice = 2ull * kSliceTargetMax * (size_t)sm_count() * 8 * 8 * 32;
-    return C * (6 * 8 + 1 + 4 + 4 + 4) + 4 * S * (U + 1) + 2 * 8 * C * U + 8 * C + 8 * C + 2 * C + slice * 12 + slice / 8 + 4 * S +
+    return C * (6 * 8 + 1 + 4 + 4) + 4 * S * (2 * U + 1) + 2 * 8 * C * U + 8 * C + 8 * C + 2 * C + slice * 12 + slice / 8 + 4 * S +
            sizeof(Counters);
 }
 
@@ -329,7 +327,6 @@ static InstView make_view(const bf_abstraction* a, bf_solve_ws* w) {
             v.uptr = a->d_uptr;
             v.uent = a->d_uent;
             v.ubits = w->ubits;
-            v.imask = w->imask;
         }
     }
     v.nwords = w->nwords;
@@ -657,7 +654,7 @@ extern "C" int bf_solve(const bf_abstraction* a, const double* G, const uint8_t*
     k_init_counters<<<1, 1, 0, st>>>(w->ctr, cap);
     BF_CUDA(cudaMemsetAsync(w->fbits, 0, 4 * w->nwords, st));
     InstView v = make_view(a, w);
-    if (v.ubits) BF_CUDA(cudaMemsetAsync(w->ubits, 0, 4 * w->nwords * U, st));
+    if (v.ubits) BF_CUDA(cudaMemsetAsync(w->ubits, 0, 8 * w->nwords * U, st));
     if (w->fc_cap > 0) BF_CUDA(cudaMemsetAsync(w->fc_tag, 0, 8 * C, st));    // no cell cached before pass 0
     k_init_costs<<<blocks_for(C, 256), 256, 0, st>>>(C, U, (const double*)dG, (const unsigned char*)dAv,
                                                      w->Gint, w->ctr);
@@ -833,8 +830,7 @@ static void set_schedule(const bf_abstraction* a, bf_solve_ws* w, const Sched& s
     w->masked = a->d_fmask != nullptr ? s.masked : 0;
     bool pf = s.pfront && a->d_uent != nullptr;
     if (pf && !w->ubits) {
-        if (cudaMalloc((void**)&w->ubits, 4 * w->nwords * w->U) != cudaSuccess ||
-            cudaMalloc((void**)&w->imask, 4 * w->C) != cudaSuccess) {
+        if (cudaMalloc((void**)&w->ubits, 8 * w->nwords * w->U) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(w->ubits);
             w->ubits = nullptr;

@@ -70,6 +70,7 @@ struct Counters {
     int done;                 // loop condition became false
     int status;               // BF_CONVERGED / BF_NEG_CYCLE / BF_ITER_CAP
     int fault;                // nonzero: a kernel gave up waiting for its copies (tile relax)
+    int ubuf;                 // per-input frontier: the buffer holding the current frontier
 };
 
 struct InstView {
@@ -102,14 +103,15 @@ struct InstView {
     int pz;                     // plane-pair dim (2 .. D - 1) of M33P, 0: none
     unsigned char* mu;          // [C]
     unsigned* fbits;            // [S]
-    // per-input frontier (per-input templates, U <= 32): the upcoming frontier
-    // as one bitmap per input (the pairs (x, u) whose box holds a changed
-    // cell), and per place of the frontier list the inputs to relax; NULL: the
-    // cell frontier fbits, every input of a frontier cell
+    // per-input frontier (per-input templates, U <= 32): one bitmap per input
+    // (the pairs (x, u) whose box holds a changed cell) in two buffers, the
+    // current frontier in buffer ctr->ubuf (relax reads it), the upcoming one
+    // in the other (marking sets it, compact takes its cells and clears the
+    // current one for the pass after); NULL: the cell frontier fbits, every
+    // input of a frontier cell
     const int* uptr;            // [P + 1] per-input templates
     const int4* uent;
-    unsigned* ubits;            // [U][S]
-    unsigned* imask;            // [C]
+    unsigned* ubits;            // [2][U][S]
     long long nwords;           // S
     int* cells;                 // [C]
     int* chg;                   // [C]
@@ -591,7 +593,8 @@ __device__ __forceinline__ void mark_template(const InstView& v, int p, int y0, 
     for (int i = b + lane; i < e; i += 32) {
         const int4 t = __ldg(te + i);
         if (skip_cov && (t.w & 1)) continue;
-        unsigned* bits = per_input ? v.ubits + (long long)(t.w >> 8) * v.nwords : v.fbits;
+        unsigned* bits = per_input ? v.ubits + ((long long)((v.ctr->ubuf ^ 1) * v.g.U) + (t.w >> 8)) * v.nwords
+                                   : v.fbits;
         const int r = y1 + t.y;
         if (r < 0 || r >= n1) continue;
         const int lo = (int)(short)(t.z & 0xFFFF), hi = t.z >> 16;
@@ -1242,6 +1245,16 @@ __device__ __forceinline__ void relax_plane(const InstView& v, long long c, bool
     }
 }
 
+// The inputs u0 <= u < u1 whose pair (c, u) is in the current per-input frontier.
+__device__ __forceinline__ unsigned input_frontier(const InstView& v, long long c, int u0, int u1) {
+    const unsigned* ub = v.ubits + (long long)v.ctr->ubuf * v.g.U * v.nwords + (c >> 5);
+    const int b = (int)(c & 31);
+    unsigned m = 0u;
+#pragma unroll 4
+    for (int u = u0; u < u1; ++u) m |= ((__ldcg(ub + (long long)u * v.nwords) >> b) & 1u) << u;
+    return m;
+}
+
 // relax_plane driven by the cell masks (fmask): per lane one 8-byte word says
 // which inputs have a box with the plane's record (the staged list applies)
 // and which have another record; only those pairs load their cost, and only
@@ -1257,7 +1270,7 @@ __device__ __forceinline__ void relax_plane_m(const InstView& v, long long c, bo
     const unsigned long long msk = act ? __ldcs(v.fmask + c) : 0ull;
     unsigned range = (u1 >= 32 ? 0xFFFFFFFFu : ((1u << u1) - 1u)) & ~((1u << u0) - 1u);
     // per-input frontier: only the pairs whose box holds a changed cell
-    if (v.imask && act) range &= __ldcs(v.imask + pos);
+    if (v.ubits && act) range &= input_frontier(v, c, u0, u1);
     {
         const unsigned taken = act ? (unsigned)__popc(range) : 0u;
         const unsigned tw = __reduce_add_sync(0xFFFFFFFFu, taken);
@@ -1396,7 +1409,7 @@ __device__ __forceinline__ void relax_plane_q(const InstView& v, long long c, bo
     const int pl = act ? plane_of_cell<D>(g, c) : -1;
     const unsigned long long msk = act ? __ldcs(v.fmask + c) : 0ull;
     unsigned range = (u1 >= 32 ? 0xFFFFFFFFu : ((1u << u1) - 1u)) & ~((1u << u0) - 1u);
-    if (v.imask && act) range &= __ldcs(v.imask + pos);
+    if (v.ubits && act) range &= input_frontier(v, c, u0, u1);
     taken += act ? __popc(range) : 0;
     const int ci = (int)c;
     const long long C = g.C;
@@ -1906,22 +1919,19 @@ __device__ __forceinline__ void compact_words(const InstView& v, int w_begin, in
     const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
     const int wd = w_begin + t;
     unsigned bits = 0;
-    // per-input frontier: the word of every input (a cell is in the frontier
-    // when some input's bit is set), kept to give each cell its input mask
-    unsigned wv[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) wv[u] = 0u;
     if (wd < w_end) {
         if (v.ubits) {
+            // per-input frontier: a cell is in the upcoming frontier when some
+            // input's bit is set; the current buffer (read by this pass's
+            // relax) is cleared for the pass after next
             const int U = v.g.U;
-#pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                if (u < U) {
-                    unsigned* pw = v.ubits + (long long)u * v.nwords + wd;
-                    wv[u] = *pw;
-                    if (wv[u]) *pw = 0u;
-                    bits |= wv[u];
-                }
+            const int cur = v.ctr->ubuf;
+            const unsigned* nx = v.ubits + (long long)(cur ^ 1) * U * v.nwords + wd;
+            unsigned* cu = v.ubits + (long long)cur * U * v.nwords + wd;
+#pragma unroll 4
+            for (int u = 0; u < U; ++u) {
+                bits |= nx[(long long)u * v.nwords];
+                cu[(long long)u * v.nwords] = 0u;
             }
         } else {
             bits = v.fbits[wd];
@@ -1955,17 +1965,6 @@ __device__ __forceinline__ void compact_words(const InstView& v, int w_begin, in
     while (bits) {
         const int b = __ffs(bits) - 1;
         bits &= bits - 1;
-        if (v.imask) {
-            unsigned m = 0u;
-            if (v.g.U <= 16) {
-#pragma unroll
-                for (int u = 0; u < 16; ++u) m |= ((wv[u] >> b) & 1u) << u;
-            } else {
-#pragma unroll
-                for (int u = 0; u < 32; ++u) m |= ((wv[u] >> b) & 1u) << u;
-            }
-            v.imask[pos] = m;
-        }
         v.cells[pos++] = (int)(cbase + b);
     }
     __syncthreads();                                      // before warp_sum / block_base are reused
@@ -1999,6 +1998,7 @@ __device__ __forceinline__ int finish_pass(const InstView& v) {
     const int next = k->nnext;
     k->ncur = next;
     k->nnext = 0;
+    if (v.ubits) k->ubuf ^= 1;
     const int cont = (next > 0 && r + 1 < k->cap) ? 1 : 0;
     if (!cont) {
         k->done = 1;
@@ -2013,6 +2013,7 @@ __device__ __forceinline__ int start_loop(const InstView& v) {
     k->nchg = 0;
     k->ncur = k->nnext;
     k->nnext = 0;
+    if (v.ubits) k->ubuf ^= 1;
     const int cont = (k->err == 0 && k->ncur > 0 && k->cap > 0) ? 1 : 0;
     if (!cont) {
         k->done = 1;
