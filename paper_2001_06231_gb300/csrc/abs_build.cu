@@ -765,27 +765,36 @@ static int build_templates(bf_abstraction* a, cudaStream_t st) {
             }
         }
     }
-    std::vector<int> ptr((size_t)P + 1, 0), uptr((size_t)P + 1, 0);
+    // per plane: the entries without the flag, then those with it;
+    // ptr[2p] = first, ptr[2p + 1] = first flagged, ptr[2p + 2] = end
+    std::vector<int> ptr(2 * (size_t)P + 1, 0), uptr(2 * (size_t)P + 1, 0);
     std::vector<int4> ent, uent;
+    std::vector<int4> flagged;
     for (long long p = 0; p < P; ++p) {
         const auto& m = tm[(size_t)p];
+        flagged.clear();
         for (auto it = m.begin(); it != m.end(); ++it) {
             const int q = it->first.first, d1 = it->first.second;
             const int lo = it->second.first, hi = it->second.second;
             auto nx = m.find({q, d1 + 1});
             const int cov = (nx != m.end() && nx->second.first <= lo && nx->second.second >= hi) ? 1 : 0;
-            ent.push_back(make_int4(q, d1, (lo & 0xFFFF) | (hi << 16), cov));
+            (cov ? flagged : ent).push_back(make_int4(q, d1, (lo & 0xFFFF) | (hi << 16), cov));
         }
-        ptr[(size_t)p + 1] = (int)ent.size();
+        ptr[2 * (size_t)p + 1] = (int)ent.size();
+        ent.insert(ent.end(), flagged.begin(), flagged.end());
+        ptr[2 * (size_t)p + 2] = (int)ent.size();
         const auto& mu_ = tu[(size_t)p];
+        flagged.clear();
         for (auto it = mu_.begin(); it != mu_.end(); ++it) {
             const int u = std::get<0>(it->first), q = std::get<1>(it->first), d1 = std::get<2>(it->first);
             const int lo = it->second.first, hi = it->second.second;
             auto nx = mu_.find(std::make_tuple(u, q, d1 + 1));
             const int cov = (nx != mu_.end() && nx->second.first <= lo && nx->second.second >= hi) ? 1 : 0;
-            uent.push_back(make_int4(q, d1, (lo & 0xFFFF) | (hi << 16), cov | (u << 8)));
+            (cov ? flagged : uent).push_back(make_int4(q, d1, (lo & 0xFFFF) | (hi << 16), cov | (u << 8)));
         }
-        uptr[(size_t)p + 1] = (int)uent.size();
+        uptr[2 * (size_t)p + 1] = (int)uent.size();
+        uent.insert(uent.end(), flagged.begin(), flagged.end());
+        uptr[2 * (size_t)p + 2] = (int)uent.size();
     }
     int *dptr = nullptr, *duptr = nullptr;
     int4 *dent = nullptr, *duent = nullptr;

@@ -241,14 +241,15 @@ struct bf_abstraction {
     // cells x = (y0 + lo .. y0 + hi, y1 + d1, q) hold pred(y) for every cell
     // y = (y0, y1, p); entries int4 {q, d1, lo & 0xFFFF | hi << 16, flags},
     // flags bit 0: row (q, d1 + 1) of the template spans lo..hi too
-    int* d_tptr;              // [nplanes + 1]
-    int4* d_tent;             // [d_tptr[nplanes]]
+    int* d_tptr;              // [2 nplanes + 1]: plane p's entries at [d_tptr[2p], d_tptr[2p + 2]),
+                              // those without the flag first, up to d_tptr[2p + 1]
+    int4* d_tent;             // [d_tptr[2 nplanes]]
     double tmpl_rows;         // mean template entries per plane
     // per-input templates (U <= 32): the same rows kept apart by input, entries
     // int4 {q, d1, lo & 0xFFFF | hi << 16, flags | u << 8} (flags bit 0: row
     // (q, d1 + 1) of input u spans lo..hi too); NULL otherwise
-    int* d_uptr;              // [nplanes + 1]
-    int4* d_uent;             // [d_uptr[nplanes]]
+    int* d_uptr;              // [2 nplanes + 1], as d_tptr
+    int4* d_uent;             // [d_uptr[2 nplanes]]
     double utmpl_rows;        // mean per-input template entries per plane
     // predecessor index [C][2*D] int16 offsets (x = y + off), empty: lo0 > hi0
     short* d_pred;

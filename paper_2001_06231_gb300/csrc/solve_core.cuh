@@ -91,7 +91,7 @@ struct InstView {
     // the plane's entry; bit 32 + u = a box with another record; or NULL
     const unsigned long long* fmask;   // [C]
     // predecessor templates per target plane (marking), or NULL: bounding boxes
-    const int* tptr;                   // [P + 1]
+    const int* tptr;                   // [2 P + 1] (entries without the flag first)
     const int4* tent;
     const double* Gint;         // [U][C] running cost, +inf on avoid cells
     long long* Vkey;            // [C]
@@ -109,7 +109,7 @@ struct InstView {
     // in the other (marking sets it, compact takes its cells and clears the
     // current one for the pass after); NULL: the cell frontier fbits, every
     // input of a frontier cell
-    const int* uptr;            // [P + 1] per-input templates
+    const int* uptr;            // [2 P + 1] per-input templates, as tptr
     const int4* uent;
     unsigned* ubits;            // [2][U][S]
     long long nwords;           // S
@@ -589,12 +589,12 @@ __device__ __forceinline__ void mark_template(const InstView& v, int p, int y0, 
     const bool per_input = v.ubits != nullptr;       // rows by input into that input's bitmap
     const int* tp = per_input ? v.uptr : v.tptr;
     const int4* te = per_input ? v.uent : v.tent;
-    const int b = __ldg(tp + p), e = __ldg(tp + p + 1);
+    // the flagged entries (row d1 + 1 spans the same range) come last
+    const int b = __ldg(tp + 2 * p), e = __ldg(tp + 2 * p + (skip_cov ? 1 : 2));
+    unsigned* ub = per_input ? v.ubits + (long long)(v.ctr->ubuf ^ 1) * v.g.U * v.nwords : v.fbits;
     for (int i = b + lane; i < e; i += 32) {
         const int4 t = __ldg(te + i);
-        if (skip_cov && (t.w & 1)) continue;
-        unsigned* bits = per_input ? v.ubits + ((long long)((v.ctr->ubuf ^ 1) * v.g.U) + (t.w >> 8)) * v.nwords
-                                   : v.fbits;
+        unsigned* bits = per_input ? ub + (long long)(t.w >> 8) * v.nwords : ub;
         const int r = y1 + t.y;
         if (r < 0 || r >= n1) continue;
         const int lo = (int)(short)(t.z & 0xFFFF), hi = t.z >> 16;
