@@ -1794,7 +1794,8 @@ __device__ __forceinline__ void table33_entry(const InstView& v, long long e) {
 // (x - a, x1 - b).  Vnew is read once over the 5 x 5 block around the cell
 // (cells outside a non-periodic edge count as kKeyMin, periodic dims wrap):
 // 3-cell row windows first, then 3-row column windows.
-__device__ __forceinline__ void windows33(const InstView& v, long long base, int x, int x1, long long out[3][3]) {
+__device__ __forceinline__ void windows33(const InstView& v, long long base, int x, int x1, long long out[3][3],
+                                          long long* row2 = nullptr) {
     const GridDesc& g = v.g;
     const int n0 = g.n[0], n1 = g.n[1];
     long long w3[5][3];
@@ -1815,6 +1816,9 @@ __device__ __forceinline__ void windows33(const InstView& v, long long base, int
             if (cin && (c < 0 || c >= n0)) c = ((c % n0) + n0) % n0;
             cv[k] = cin ? v.Vnew[base + (long long)r * n0 + c] : kKeyMin;
         }
+        if (row2 && i == 2)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) row2[k] = cv[k];
 #pragma unroll
         for (int a = 0; a < 3; ++a) w3[i][a] = max(cv[2 - a], max(cv[3 - a], cv[4 - a]));
     }
@@ -1869,20 +1873,33 @@ __device__ __forceinline__ void refresh_tables(const InstView& v, long long y) {
     const long long rq = (long long)grid_div(g, 0, (unsigned)y);
     const long long row = rq * n0;
     const int x = (int)(y - row);
-    for (int j = 0; j < 3 && j < n0; ++j) {
-        int xe = x - j;
-        if (xe < 0) {
-            if (!g.periodic[0]) break;
-            xe += n0;
+    if (!v.M33 || v.rmask) {
+        for (int j = 0; j < 3 && j < n0; ++j) {
+            int xe = x - j;
+            if (xe < 0) {
+                if (!g.periodic[0]) break;
+                xe += n0;
+            }
+            table_entry(v, row + xe);
         }
-        table_entry(v, row + xe);
     }
     if (v.M33) {
         const int n1 = g.n[1];
         const int x1 = (int)(rq - (long long)grid_div(g, 1, (unsigned)rq) * n1);
         const long long base = row - (long long)x1 * n0;
-        long long mid[3][3];
-        windows33(v, base, x, x1, mid);
+        long long mid[3][3], r2[5];
+        windows33(v, base, x, x1, mid, r2);
+        // M2 / M3 at x - j from y's row of the block (cells x - 2 .. x + 2)
+        for (int j = 0; j < 3 && j < n0; ++j) {
+            int xe = x - j;
+            if (xe < 0) {
+                if (!g.periodic[0]) break;
+                xe += n0;
+            }
+            const long long a = r2[2 - j], b = r2[3 - j], c3 = r2[4 - j];
+            v.M2[row + xe] = max(a, b);
+            v.M3[row + xe] = max(a, max(b, c3));
+        }
         write33(v, v.M33, base, x, x1, mid, mid);
         if (v.M33P) {
             // the pair entries holding y's plane: (plane z, z + 1) and (z - 1, z)
