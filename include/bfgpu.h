@@ -387,15 +387,16 @@ BF_API int bf_solve_batch(int32_t n, const bf_abstraction *const *abs, const dou
 /* bf_tune_batch -- pick the batched form's schedule by timing whole
  * bf_solve_batch calls on these instances (arguments as bf_solve_batch, no
  * result arrays): whether relax marks the next frontier itself, the 3 x 3
- * window table, the plane lookup lists, the predecessor templates and two
- * inputs per relax iteration (one at a time, keeping the others at the best so
- * far, two rounds; each candidate solved three times).  The fastest schedule
+ * window table, the plane lookup lists, the predecessor templates, two
+ * inputs per relax iteration and the relax by cell masks with the pairs queued
+ * over the lanes (one at a time, keeping the others at the best so far, two
+ * rounds; each candidate solved three times).  The fastest schedule
  * is stored in every given abstraction and used by later bf_solve_batch calls
  * and by the server's engine (a group of instances that share a dimension and
  * storage form takes the schedule of its first instance).  In *out: fuse_mark
  * (-1: by predecessor-box size, the default), window33, plane_lists,
- * templates, pair_inputs, candidates, best_ms and default_ms; the other fields
- * are 0.  Results never depend on the schedule.  Errors: as bf_solve_batch. */
+ * templates, pair_inputs, cell_masks (0 or 2), candidates, best_ms and
+ * default_ms; the other fields are 0.  Results never depend on the schedule.  Errors: as bf_solve_batch. */
 BF_API int bf_tune_batch(int32_t n, const bf_abstraction *const *abs, const double *const *G,
                   const uint8_t *const *target, const uint8_t *const *avoid,
                   const double *const *terminal, int64_t max_iters, bf_tune_result *out, void *stream);
@@ -403,7 +404,8 @@ BF_API int bf_tune_batch(int32_t n, const bf_abstraction *const *abs, const doub
 /* bf_set_batch_schedule -- put a batched-form schedule in force on an
  * abstraction without timing: fuse_mark (-1: relax marks when the
  * predecessor boxes are small, 0: a propagate launch, 1: relax marks),
- * window33, plane_lists, templates and pair_inputs of *sched are read.  The
+ * window33, plane_lists, templates, pair_inputs and cell_masks (nonzero: the
+ * pair-queue relax) of *sched are read.  The
  * handle is modified; it must not be in use by a running batch or server.
  * Results never depend on the schedule.  Returns BF_OK or BF_ERR_INVALID. */
 BF_API int bf_set_batch_schedule(bf_abstraction *abs, const bf_tune_result *sched);

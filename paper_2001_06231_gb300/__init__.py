@@ -410,11 +410,13 @@ def bf_tune_batch(abstractions, Gs, targets=None, avoids=None, terminals=None, m
     return {k: getattr(res, k) for k, _ in res._fields_}
 
 
-def bf_set_batch_schedule(abstraction, fuse_mark=-1, window33=1, plane_lists=1, templates=1, pair_inputs=1):
+def bf_set_batch_schedule(abstraction, fuse_mark=-1, window33=1, plane_lists=1, templates=1, pair_inputs=1,
+                          cell_masks=0):
     """Put a batched-form schedule in force on this abstraction (no timing)."""
     s = TuneResult()
     s.fuse_mark, s.window33, s.plane_lists, s.templates, s.pair_inputs = (fuse_mark, window33, plane_lists,
                                                                          templates, pair_inputs)
+    s.cell_masks = cell_masks
     _check(lib().bf_set_batch_schedule(abstraction.handle, ctypes.byref(s)))
 
 

@@ -262,6 +262,36 @@ __global__ void __launch_bounds__(256, PAIR ? 3 : 4) k_b_relax_pl(BatchDev b, in
     }
 }
 
+// The group's relax by cell masks with the pairs queued over the lanes
+// (relax_plane_q; every instance of the group has the masks and lists).  The
+// stage is emptied before each chunk: consecutive chunks of a warp may belong
+// to different instances.
+template <int D, bool MARK, int UM, bool R2>
+__global__ void __launch_bounds__(UM == 16 ? 256 : 128, 3) k_b_relax_pq(BatchDev b, int g) {
+    const int beg = b.gbeg[g], end = b.gbeg[g + 1];
+    if (beg >= end) return;
+    extern __shared__ __align__(16) unsigned char b_pair_smem[];
+    PairStage<UM>* st = reinterpret_cast<PairStage<UM>*>(b_pair_smem) + (threadIdx.x >> 5);
+    const int base = b.scan[beg], total = b.scan[end] - base;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    long long taken = 0;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < total; item += nwarps) {
+        const int pos = base + item;
+        const int i = find_instance(b.scan, beg, end, pos);
+        const InstView& v = b.views[i];
+        const int ch = pos - b.scan[i];
+        int exact = 0;
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) st->plane = -1;
+        __syncwarp();
+        const int r = relax_chunk<D, kBoxCompact, false, MARK, false, R2 ? 6 : 5, UM>(
+            v, ch << 5, v.ctr->ncur - (ch << 5), v.ctr->round, &exact, st, &taken);
+        if ((threadIdx.x & 31) == 0 && r)
+            atomicAdd((unsigned long long*)&v.ctr->relaxed, (unsigned long long)r);
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_b_propagate(BatchDev b, int g) {
     const int beg = b.gbeg[g], end = b.gbeg[g + 1];
@@ -422,6 +452,7 @@ int Engine::add(const bf_abstraction* a, const double* G, const unsigned char* t
     const int bs = a->bsched >= 0 ? a->bsched : kBsDefault;
     if ((bs & kBsWindow33) && a->g.D >= 2) v.M33 = reinterpret_cast<long long*>(m + o_m33);
     if ((bs & kBsPlane) && a->d_poffs[0]) v.poffs = a->d_poffs[v.M33 ? 1 : 0];
+    if ((bs & kBsQueue) && a->d_fmask) v.fmask = a->d_fmask;
     if ((bs & kBsTemplates) && a->d_tent) {
         v.tptr = a->d_tptr;
         v.tent = a->d_tent;
@@ -505,6 +536,8 @@ int Engine::rebuild() {
             if (group_fixed_mark_[ng]) group_mark_[ng] = (bs & kBsMark) != 0;
             group_plane_[ng] = (bs & kBsPlane) != 0 && group_fmt_[ng] == kBoxCompact && group_D_[ng] >= 2;
             group_pair_[ng] = (bs & kBsPair) != 0;
+            group_queue_[ng] = group_plane_[ng] && (bs & kBsQueue) != 0;
+            group_wide_[ng] = false;
             dev_.gbeg[ng] = i;
             ++ng;
         }
@@ -513,6 +546,8 @@ int Engine::rebuild() {
         const double rows = insts_[i]->view.tent ? a->tmpl_rows : a->pred_rows;
         if (!group_fixed_mark_[ng - 1] && rows > kFuseMarkRowsBatch) group_mark_[ng - 1] = false;
         if (!a->d_poffs[0] || a->g.U > kPlaneUMax) group_plane_[ng - 1] = false;
+        if (!group_plane_[ng - 1] || !insts_[i]->view.fmask) group_queue_[ng - 1] = false;
+        if (a->g.U > 16) group_wide_[ng - 1] = true;
     }
     dev_.ngroups = ng;
     dev_.gbeg[ng] = n;
@@ -566,6 +601,29 @@ static void launch_relax_pl(const BatchDev& b, int g, bool pair, cudaStream_t st
     else k_b_relax_pl<D, MARK, false><<<blocks, 256, sm, st>>>(b, g);
 }
 
+template <int D, bool MARK, int UM, bool R2>
+static void launch_relax_pq_t(const BatchDev& b, int g, cudaStream_t st) {
+    const size_t sm = (UM == 16 ? 8 : 4) * sizeof(PairStage<UM>);
+    static bool once = false;
+    if (!once) {
+        cudaFuncSetAttribute((const void*)k_b_relax_pq<D, MARK, UM, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+        once = true;
+    }
+    k_b_relax_pq<D, MARK, UM, R2><<<n_sms() * 3, UM == 16 ? 256 : 128, sm, st>>>(b, g);
+}
+
+template <int D, bool MARK>
+static void launch_relax_pq(const BatchDev& b, int g, bool wide, bool pair, cudaStream_t st) {
+    if (wide) {
+        if (pair) launch_relax_pq_t<D, MARK, 32, true>(b, g, st);
+        else launch_relax_pq_t<D, MARK, 32, false>(b, g, st);
+    } else {
+        if (pair) launch_relax_pq_t<D, MARK, 16, true>(b, g, st);
+        else launch_relax_pq_t<D, MARK, 16, false>(b, g, st);
+    }
+}
+
 template <int D, bool MARK>
 static void launch_relax_m(const BatchDev& b, int g, int fmt, int blocks, cudaStream_t st) {
     switch (fmt) {
@@ -577,9 +635,14 @@ static void launch_relax_m(const BatchDev& b, int g, int fmt, int blocks, cudaSt
 }
 
 template <int D>
-static void launch_relax(const BatchDev& b, int g, int fmt, bool mark, bool plane, bool pair, int blocks,
-                         cudaStream_t st) {
+static void launch_relax(const BatchDev& b, int g, int fmt, bool mark, bool plane, bool pair, bool queue, bool wide,
+                         int blocks, cudaStream_t st) {
     if constexpr (D >= 2) {
+        if (queue) {
+            if (mark) launch_relax_pq<D, true>(b, g, wide, pair, st);
+            else launch_relax_pq<D, false>(b, g, wide, pair, st);
+            return;
+        }
         if (plane) {
             if (mark) launch_relax_pl<D, true>(b, g, pair, st);
             else launch_relax_pl<D, false>(b, g, pair, st);
@@ -598,11 +661,12 @@ static void launch_prop(const BatchDev& b, int g, int blocks, cudaStream_t st) {
 void Engine::launch_pass(cudaGraphConditionalHandle h, int use_graph) {
     for (int g = 0; g < dev_.ngroups; ++g) {
         const bool mark = group_mark_[g], pl = group_plane_[g], pr = group_pair_[g];
+        const bool q = group_queue_[g], wd = group_wide_[g];
         switch (group_D_[g]) {
-            case 1: launch_relax<1>(dev_, g, group_fmt_[g], mark, false, false, relax_blocks_, st_); break;
-            case 2: launch_relax<2>(dev_, g, group_fmt_[g], mark, pl, pr, relax_blocks_, st_); break;
-            case 3: launch_relax<3>(dev_, g, group_fmt_[g], mark, pl, pr, relax_blocks_, st_); break;
-            default: launch_relax<4>(dev_, g, group_fmt_[g], mark, pl, pr, relax_blocks_, st_); break;
+            case 1: launch_relax<1>(dev_, g, group_fmt_[g], mark, false, false, false, false, relax_blocks_, st_); break;
+            case 2: launch_relax<2>(dev_, g, group_fmt_[g], mark, pl, pr, q, wd, relax_blocks_, st_); break;
+            case 3: launch_relax<3>(dev_, g, group_fmt_[g], mark, pl, pr, q, wd, relax_blocks_, st_); break;
+            default: launch_relax<4>(dev_, g, group_fmt_[g], mark, pl, pr, q, wd, relax_blocks_, st_); break;
         }
     }
     k_b_plan<<<1, 1024, 0, st_>>>(dev_, 1, h, use_graph);
@@ -868,9 +932,9 @@ extern "C" int bf_tune_batch(int32_t n, const bf_abstraction* const* abs, const 
     const double default_ms = best;
     // coordinate descent over the schedule bits, two rounds; the marking
     // dimension times both fixed choices against marking by box size
-    const int bits[5] = {kBsMark, kBsWindow33, kBsPlane, kBsTemplates, kBsPair};
+    const int bits[6] = {kBsMark, kBsWindow33, kBsPlane, kBsTemplates, kBsPair, kBsQueue};
     for (int round = 0; round < 2 && rc == BF_OK; ++round)
-        for (int k = 0; k < 5 && rc == BF_OK; ++k) {
+        for (int k = 0; k < 6 && rc == BF_OK; ++k) {
             const int base = b;
             int cands[2];
             if (k == 0) {
@@ -910,6 +974,7 @@ extern "C" int bf_tune_batch(int32_t n, const bf_abstraction* const* abs, const 
     out->plane_lists = (bs & kBsPlane) ? 1 : 0;
     out->templates = (bs & kBsTemplates) ? 1 : 0;
     out->pair_inputs = (bs & kBsPair) ? 1 : 0;
+    out->cell_masks = (bs & kBsQueue) ? 2 : 0;
     out->candidates = tried;
     out->best_ms = best;
     out->default_ms = default_ms;
@@ -926,7 +991,8 @@ extern "C" int bf_set_batch_schedule(bf_abstraction* a, const bf_tune_result* sc
         return BF_ERR_INVALID;
     }
     int bs = (sched->window33 ? kBsWindow33 : 0) | (sched->plane_lists ? kBsPlane : 0) |
-             (sched->templates ? kBsTemplates : 0) | (sched->pair_inputs ? kBsPair : 0);
+             (sched->templates ? kBsTemplates : 0) | (sched->pair_inputs ? kBsPair : 0) |
+             (sched->cell_masks ? kBsQueue : 0);
     if (sched->fuse_mark == 1) bs |= kBsMark;
     if (sched->fuse_mark == -1) bs |= kBsMarkAuto;
     a->bsched = bs;

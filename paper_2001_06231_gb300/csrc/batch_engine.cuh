@@ -109,6 +109,8 @@ private:
     bool group_fixed_mark_[kMaxGroups] = {};   // ... as the first instance's batched schedule says
     bool group_plane_[kMaxGroups] = {};  // relax reads the plane lookup lists (plane kernel)
     bool group_pair_[kMaxGroups] = {};   // ... two inputs per iteration
+    bool group_queue_[kMaxGroups] = {};  // ... by cell masks, pairs queued over the lanes
+    bool group_wide_[kMaxGroups] = {};   // ... some instance has more than 16 inputs
     // bounded-step graphs of the current instance set, by pass count
     cudaGraphExec_t step_exec_[2] = {nullptr, nullptr};
     int step_passes_[2] = {0, 0};

@@ -266,6 +266,7 @@ constexpr int kBsTemplates = 4;   // marking reads the predecessor templates
 constexpr int kBsPair = 8;        // plane relax takes two inputs per iteration
 constexpr int kBsMark = 16;       // relax marks the next frontier (else a propagate launch)
 constexpr int kBsMarkAuto = 32;   // ... when the group's predecessor boxes are small (kBsMark ignored)
+constexpr int kBsQueue = 64;      // plane relax by cell masks, the pairs queued over the lanes
 constexpr int kBsDefault = kBsWindow33 | kBsPlane | kBsTemplates | kBsPair | kBsMarkAuto;
 
 namespace bfh {

@@ -98,12 +98,16 @@ def test_batch_full_size_64_uneven_unicycles():
     dict(fuse_mark=0, window33=1, plane_lists=1, templates=0, pair_inputs=1),
     dict(fuse_mark=0, window33=0, plane_lists=0, templates=1, pair_inputs=0),
     dict(fuse_mark=1, window33=0, plane_lists=1, templates=0, pair_inputs=1),
+    dict(fuse_mark=0, window33=1, plane_lists=1, templates=1, pair_inputs=1, cell_masks=2),
+    dict(fuse_mark=1, window33=1, plane_lists=1, templates=1, pair_inputs=0, cell_masks=2),
+    dict(fuse_mark=-1, window33=0, plane_lists=1, templates=0, pair_inputs=1, cell_masks=2),
 ])
 def test_batch_schedules_equal_solo_and_oracle(sched):
     """The batched form's schedules (3 x 3 window table, plane lookup lists and
     their kernel, predecessor templates, two inputs per iteration, marking in
-    relax or a propagate launch): every instance equal to its solo solve and
-    the instances on the oracle's boxes equal to the oracle."""
+    relax or a propagate launch, the relax by cell masks with the pairs queued
+    over the lanes): every instance equal to its solo solve and the instances
+    on the oracle's boxes equal to the oracle."""
     ws = [wl.unicycle3d(n=(40, 36, 16), n_obstacles=5, seed=1),
           wl.fire4d(n=(30, 28, 24, 6), target=((50.0, 350.0), (50.0, 300.0), (-0.4, 0.4), (10.0, 15.0))),
           wl.unicycle3d(n=(70, 64, 24), n_obstacles=12, seed=2, cost_c=0.7),
