@@ -38,8 +38,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "(cell,input) relaxations/s"
 UNIT = "relaxations/s"
-PROFILES = {"unicycle3d": os.path.join(ROOT, "profiles", "k_relax_pl_unicycle3d_200x200x64.txt"),
-            "fire4d": os.path.join(ROOT, "profiles", "k_relax_pl_fire4d_100x100x36x8.txt")}
+PROFILES = {"unicycle3d": os.path.join(ROOT, "profiles", "k_relax_pq_unicycle3d_200x200x64.txt"),
+            "fire4d": os.path.join(ROOT, "profiles", "k_relax_pq_fire4d_100x100x36x8.txt")}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2001_06231_gb300", "csrc", f)
                   for f in ("solve_core.cuh", "solve.cu", "solve_plane.cu", "bf_internal.cuh", "dynamics.cuh")]
 FIRE_TARGET_WIDE = ((50.0, 250.0), (50.0, 150.0), (-0.5235987755982988, 0.5235987755982988), (10.0, 15.0))
@@ -372,8 +372,9 @@ def ours(args, rank, world, local_rank):
     masked = bool(tuned and tuned.get("cell_masks") and tuned.get("plane_lists"))
     bpp = algorithmic_bytes_per_pair(A, masked)
     exec_bytes_per_launch = executed * bpp / max(1, passes)
-    # ncu DRAM bytes of the profiled relax launch, per executed pair, scaled to
-    # this run's mean launch -- only for the kernel sources and relax form captured
+    # ncu DRAM bytes of the profiled relax launch, per relaxed (frontier) cell,
+    # scaled to this run's mean launch -- only for the kernel sources and relax
+    # form captured
     traffic = None
     prof = PROFILES.get(args.workload)
     if prof and os.path.exists(prof) and A.mode == bf.MODE_STORED and tuned:
@@ -383,7 +384,7 @@ def ours(args, rank, world, local_rank):
         same_form = bool(form) and all(str(tuned.get(k)) == v for k, v in form.items())
         if kv.get("kernel_hash") == kernel_hash() and same_form:
             try:
-                traffic = float(kv["dram_bytes_per_executed_pair"]) * executed / max(1, passes)
+                traffic = float(kv["dram_bytes_per_relaxed_cell"]) * rt["stats"]["relaxed_cells"] / max(1, passes)
             except (KeyError, ValueError):
                 traffic = None
 
