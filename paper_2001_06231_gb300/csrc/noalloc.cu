@@ -4,14 +4,13 @@
 //
 // All working state lives in g_scratch, a file-scope device array of fixed
 // size.  Host code must not use the name g_scratch as an address (on the host
-// it only stands in for the symbol); the device address is looked up once
-// per device with cudaGetSymbolAddress and passed to the kernels.  The passes
+// it only stands in for the symbol); the device address is looked up on each
+// call with cudaGetSymbolAddress and passed to the kernels.  The passes
 // are the same device routines as bf_solve (solve_core.cuh), launched from
 // the host in groups of kPassesPerCheck, with one read of the counters per
 // group; kernels launched after the loop condition turned false return at
 // once.
 #include <cstring>
-#include <mutex>
 
 #include "solve_core.cuh"
 
@@ -20,30 +19,17 @@ using namespace bfk;
 namespace {
 
 constexpr size_t kScratchBytes = BF_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 constexpr int kPassesPerCheck = 8;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mtx;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (looked up once).
+// Device address of g_scratch on the current device, looked up on every call
+// (a cached address would go stale when the context is reset).
 int scratch_base(void** out) {
-    int dev = 0;
-    BF_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        bfh::set_error("bf_solve_noalloc: device %d out of range", dev);
-        return BF_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_mtx);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return bfh::cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return bfh::cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
+    *out = p;
     return BF_OK;
 }
 
