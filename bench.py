@@ -24,6 +24,7 @@ does not shard): weak scaling, value = all ranks' relaxations / max time.
 """
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -46,10 +47,15 @@ FIRE_TARGET_WIDE = ((50.0, 250.0), (50.0, 150.0), (-0.5235987755982988, 0.523598
 
 
 def kernel_hash():
+    """Hash of the relax sources' code (comments and blank space left out), so
+    that a profile stays matched to the code it was captured on."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

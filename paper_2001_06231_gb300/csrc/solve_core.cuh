@@ -44,6 +44,13 @@
 // systems), every lookup is one warp load at a lane-independent offset from
 // each lane's cell and the loops are warp-uniform.  Other warps walk each
 // lane's box cell by cell.
+//
+// Plane relax forms (abstractions with a plane shape table): the lists of the
+// plane a warp's cells lie on are staged in shared memory; relax_plane reads
+// every record, relax_plane_m the per-cell input masks (inputs in turn), and
+// relax_plane_q queues the (lane, input) pairs the lists serve over the lanes,
+// so that with the per-input frontier (one bitmap per input, marked from
+// per-input templates) only pairs whose box holds a changed cell cost work.
 #pragma once
 #include <type_traits>
 
