@@ -113,3 +113,27 @@ def test_box_extent_division_by_multiply_high_is_exact():
         ts = ts[ts < top]
         q = ((ts << np.uint64(1)) * m) >> np.uint64(32)
         assert np.array_equal(q, ts // np.uint64(d)), d
+
+
+def test_bench_kernel_hash_ignores_comments_and_profiles_parse(tmp_path, monkeypatch):
+    """bench.py matches a committed ncu summary to the relax code it was taken
+    on by a hash of the sources without comments: a comment edit keeps the
+    hash, a code edit changes it; every summary bench.py names carries the
+    keys it reads (kernel hash, relax form)."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cuh"
+    src.write_text("// header\nint f(int x) { return x + 1; }  /* note */\n")
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", [str(src)])
+    h0 = bench.kernel_hash()
+    src.write_text("// another header\n\nint f(int x) {   return x + 1; }\n")
+    assert bench.kernel_hash() == h0
+    src.write_text("int f(int x) { return x + 2; }\n")
+    assert bench.kernel_hash() != h0
+    for path in bench.PROFILES.values():
+        kv = {k.strip(): v.strip() for k, v in (l.split(":", 1) for l in open(path)
+                                                  if ":" in l and not l.startswith("#"))}
+        assert re.fullmatch(r"[0-9a-f]{16}", kv["kernel_hash"]), path
+        form = dict(x.split("=") for x in kv["relax_form"].split())
+        assert {"plane_lists", "cell_masks", "input_frontier"} <= set(form), path
