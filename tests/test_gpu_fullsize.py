@@ -13,6 +13,9 @@ own builder is compared with the oracle's on every box.
   Bellman checker runs on every cell.
 * Fire model as stated with tau 1 s and the narrow landing box: a degenerate
   instance (a few passes, few finite cells), compared the same way.
+* Each also with the relax forms the tuner picks at these sizes (cell masks,
+  the pairs queued over the lanes, the per-input frontier; marking in its own
+  launch or in relax), against the same oracle solve.
 """
 import math
 
@@ -69,9 +72,30 @@ def test_unicycle_full_size_bit_exact():
     assert np.all(res["trace"][:k, 0] >= ref["f1"][:k])
     nbad, first = oracle.bellman_check(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid, res["V"], res["mu"])
     assert nbad == 0, first
+    tuned_forms_match(A, w, ref)
     # the value is finite on the target (0) and a decent share of the state space
     assert np.all(res["V"][w.target.astype(bool)] == 0.0)
     assert np.isfinite(res["V"]).sum() > 0.5 * w.ncells
+
+
+def tuned_forms_match(A, w, ref):
+    """The relax forms bf_tune picks at the measured sizes (cell masks, the
+    pairs queued over the lanes, the per-input frontier; marking in its own
+    launch or in relax) to the fixed point: the oracle's V, mu, pass count and
+    per-pass changed counts, with fewer pairs taken up than every input of the
+    frontier cells."""
+    k = ref["iters"]
+    for fuse in (0, 1):
+        bf.bf_set_schedule(A, slice_target=0, fuse_mark=fuse, window33=1, plane_lists=1, templates=1,
+                           pair_inputs=1, cell_masks=2, input_frontier=1)
+        q = gpu_solve(A, w, trace_cap=8192)
+        assert q["status"] == ref["status"] and q["iters"] == k, fuse
+        assert same(q["V"], ref["V"]) and same(q["mu"], ref["mu"]), fuse
+        assert same(q["trace"][:k, 1], ref["changed"][:k]), fuse
+        assert np.all(q["trace"][:k, 0] >= ref["f1"][:k]), fuse
+        assert q["stats"]["executed_pairs"] < int(ref["f1"].sum()) * w.ninputs, fuse
+        print("tuned form, fuse %d: %d pairs taken up of %d canonical"
+              % (fuse, q["stats"]["executed_pairs"], int(ref["f1"].sum()) * w.ninputs))
 
 
 def fire_parity(w):
@@ -94,6 +118,7 @@ def fire_parity(w):
     assert same(cnt["trace"][:k, 3], ref["f1"][:k])
     nbad, first = oracle.bellman_check(w.grid.n, w.grid.periodic, boxes, w.G, T, w.avoid, res["V"], res["mu"])
     assert nbad == 0, first
+    tuned_forms_match(A, w, ref)
     # negative costs over the fire; avoid cells stay +inf; V <= 0 on the target
     assert (w.G < 0).any()
     assert np.all(np.isinf(res["V"][w.avoid.astype(bool)]))
